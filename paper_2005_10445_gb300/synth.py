@@ -1,0 +1,228 @@
+"""Seeded synthetic inputs for the acquisition search.
+
+This module only *makes* inputs: tag codes, complex baseband streams with
+additive white Gaussian noise, and tag transmissions injected at a known
+delay, carrier offset, phase and SNR.  It contains none of the search's
+arithmetic (no correlation, no FFT, no peak search), so that both the CUDA
+path and the FP64 oracle can be fed from it without sharing method code.
+
+Signal model (Section 2: packets of pseudorandom bits at about 1 Mb/s,
+received as complex samples at 8 MS/s; Section 3 step 6: the replica is a
+noise-free copy of the transmission):
+
+* a tag code is a sequence of +/-1 chips; a transmission of code ``c`` at
+  integer delay ``d`` occupies samples ``d .. d + chips*sps - 1`` and holds
+  chip ``i`` for ``sps`` consecutive samples;
+* the transmission is rotated by a carrier offset ``f`` (Hz) and a phase,
+  ``A * exp(j(2*pi*f*t/fs + phi)) * chip[(t-d)//sps]`` for absolute sample ``t``;
+* noise is complex AWGN with standard deviation ``sigma`` per component
+  (int16-range, sigma = 2048 by default) and the amplitude follows the
+  per-complex-sample SNR, ``A = sqrt(2 sigma^2 10^(snr_db/10))``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state: int, n: int) -> np.ndarray:
+    """``n`` outputs of Vigna's splitmix64 generator started at ``state``.
+
+    Published definition: state += 0x9E3779B97F4A7C15; z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9; z = (z ^ (z >> 27)) *
+    0x94D049BB133111EB; return z ^ (z >> 31)  (all mod 2^64).
+    """
+    out = np.empty(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        s = np.uint64(state & MASK64)
+        idx = np.arange(1, n + 1, dtype=np.uint64)
+        z = s + idx * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        out[:] = z ^ (z >> np.uint64(31))
+    return out
+
+
+def random_chips(n_chips: int, seed: int) -> np.ndarray:
+    """+/-1 chips (int8) from the low bit of splitmix64 outputs."""
+    bits = splitmix64(seed, n_chips) & np.uint64(1)
+    return (1 - 2 * bits.astype(np.int8)).astype(np.int8)
+
+
+def lfsr_chips(seed: int = 1, degree: int = 10, taps: Sequence[int] = (10, 7)) -> np.ndarray:
+    """One period (2^degree - 1 chips) of a Fibonacci LFSR as +/-1 int8.
+
+    The default polynomial x^10 + x^7 + 1 is primitive, so the sequence is a
+    maximal-length (m-)sequence of 1023 chips.  ``seed`` is the nonzero initial
+    register state.
+    """
+    n = (1 << degree) - 1
+    reg = seed & n
+    if reg == 0:
+        raise ValueError("LFSR seed must be nonzero")
+    out = np.empty(n, dtype=np.int8)
+    for i in range(n):
+        bit = 0
+        for t in taps:
+            bit ^= (reg >> (degree - t)) & 1
+        out[i] = 1 - 2 * (reg & 1)
+        reg = (reg >> 1) | (bit << (degree - 1))
+    return out
+
+
+@dataclasses.dataclass
+class Tag:
+    code: int
+    delay: float          # samples from stream start (integer for parity configs)
+    freq_hz: float        # carrier offset actually injected
+    bin: int              # nearest grid bin index (for bookkeeping)
+    snr_db: float
+    phase: float
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    x: np.ndarray                 # complex64 [S]
+    chips: List[np.ndarray]       # list of int8 +/-1 arrays
+    sps: int
+    fs_hz: float
+    freqs_hz: np.ndarray          # float64 [K]
+    fft_len: int                  # N (0 = library default per code)
+    tags: List[Tag]
+    sigma: float
+
+    @property
+    def n_samples(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def chips_concat(self) -> np.ndarray:
+        return np.concatenate(self.chips).astype(np.int8)
+
+    @property
+    def chips_per_code(self) -> np.ndarray:
+        return np.array([len(c) for c in self.chips], dtype=np.int32)
+
+    def iq(self) -> np.ndarray:
+        """Interleaved float32 (re, im) view, shape [S, 2]."""
+        return self.x.view(np.float32).reshape(-1, 2)
+
+
+def awgn(n: int, sigma: float, rng: np.random.Generator) -> np.ndarray:
+    z = rng.standard_normal(2 * n, dtype=np.float64) * sigma
+    return (z[0::2] + 1j * z[1::2]).astype(np.complex64)
+
+
+def tag_amplitude(snr_db: float, sigma: float) -> float:
+    return math.sqrt(2.0 * sigma * sigma * 10.0 ** (snr_db / 10.0))
+
+
+def inject(x: np.ndarray, chips: np.ndarray, sps: int, fs_hz: float, tag: Tag, sigma: float,
+           amplitude: Optional[float] = None) -> None:
+    """Add one transmission of ``chips`` to ``x`` in place (float64 arithmetic).
+
+    The receiver's sample ``t`` is modelled as the average of the chip
+    waveform over the sample interval [t, t+1) (an integrate-and-dump front
+    end), so a fractional delay produces a partial sample at each chip edge
+    and carries sub-sample timing.  For an integer delay every interval lies
+    inside one chip and sample ``t`` holds chip ``(t - delay) // sps`` exactly.
+    The carrier is evaluated at the sample instant ``t``.
+    """
+    S = x.shape[0]
+    L = len(chips) * sps
+    A = tag_amplitude(tag.snr_db, sigma) if amplitude is None else amplitude
+    t0 = int(math.floor(tag.delay))
+    t = np.arange(max(t0, 0), min(t0 + L + 1, S), dtype=np.int64)
+    if t.size == 0:
+        return
+    ch = np.asarray(chips, dtype=np.float64)
+    cum = np.concatenate([[0.0], np.cumsum(ch)]) * sps   # integral at chip edges
+
+    def integral(u):
+        u = np.clip(u, 0.0, float(L))
+        i = np.minimum(np.floor(u / sps).astype(np.int64), len(ch) - 1)
+        return cum[i] + (u - i * sps) * ch[i]
+
+    rel = t.astype(np.float64) - tag.delay
+    val = integral(rel + 1.0) - integral(rel)
+    ph = 2.0 * math.pi * tag.freq_hz * t.astype(np.float64) / fs_hz + tag.phase
+    x[t] += (A * val * np.exp(1j * ph)).astype(np.complex64)
+
+
+def freq_grid(lo_hz: float, hi_hz: float, step_hz: float) -> np.ndarray:
+    k = int(round((hi_hz - lo_hz) / step_hz)) + 1
+    return lo_hz + step_hz * np.arange(k, dtype=np.float64)
+
+
+def tiny(seed: int = 1, snr_db: float = -10.0, sigma: float = 2048.0) -> Workload:
+    """One 16384-sample window, one 1023-chip LFSR code at 2 samples/chip,
+    5 bins of 500 Hz at 2 MS/s, one tag at -10 dB."""
+    rng = np.random.default_rng(seed)
+    fs, sps, N = 2e6, 2, 16384
+    chips = lfsr_chips(seed=seed if seed > 0 else 1)
+    L = len(chips) * sps
+    freqs = freq_grid(-1000.0, 1000.0, 500.0)
+    x = awgn(N, sigma, rng)
+    hop = N - L
+    delay = int(rng.integers(0, hop + 1))
+    b = int(rng.integers(0, len(freqs)))
+    f = float(freqs[b] + rng.uniform(-50.0, 50.0))
+    tag = Tag(code=0, delay=float(delay), freq_hz=f, bin=b, snr_db=snr_db,
+              phase=float(rng.uniform(0, 2 * math.pi)))
+    inject(x, chips, sps, fs, tag, sigma)
+    return Workload("tiny: 1 window x 16384, 1 code x 1023 chips, sps 2, 5 bins",
+                    x, [chips], sps, fs, freqs, N, [tag], sigma)
+
+
+def realistic(seed: int = 2, seconds: float = 1.0, n_codes: int = 16, n_chips: int = 8192,
+              sps: int = 8, fs_hz: float = 8e6, n_tags: int = 40, snr_range=(-20.0, 0.0),
+              freqs_hz: Optional[np.ndarray] = None, sigma: float = 2048.0,
+              jitter_hz: float = 12.0, min_same_code_gap: Optional[int] = None,
+              fft_len: int = 0) -> Workload:
+    """1 s of 8 MS/s complex noise, 16 codes x 8192 chips at 8 samples/chip,
+    31 bins of 1 kHz over +/-15 kHz, 40 tags with SNR U[-20, 0] dB."""
+    rng = np.random.default_rng(seed)
+    S = int(round(seconds * fs_hz))
+    L = n_chips * sps
+    N = fft_len if fft_len else 2 * (1 << (L - 1).bit_length())
+    freqs = freq_grid(-15000.0, 15000.0, 1000.0) if freqs_hz is None else np.asarray(freqs_hz, np.float64)
+    chips = [random_chips(n_chips, seed * 1_000_003 + c) for c in range(n_codes)]
+    x = awgn(S, sigma, rng)
+    gap = 2 * N if min_same_code_gap is None else min_same_code_gap
+    tags: List[Tag] = []
+    placed = {c: [] for c in range(n_codes)}
+    tries = 0
+    while len(tags) < n_tags and tries < 100000:
+        tries += 1
+        c = int(rng.integers(0, n_codes))
+        d = int(rng.integers(0, S - L + 1))
+        if any(abs(d - p) < gap for p in placed[c]):
+            continue
+        b = int(rng.integers(0, len(freqs)))
+        f = float(freqs[b] + rng.uniform(-jitter_hz, jitter_hz))
+        snr = float(rng.uniform(*snr_range))
+        tg = Tag(code=c, delay=float(d), freq_hz=f, bin=b, snr_db=snr,
+                 phase=float(rng.uniform(0, 2 * math.pi)))
+        placed[c].append(d)
+        tags.append(tg)
+        inject(x, chips[c], sps, fs_hz, tg, sigma)
+    return Workload(f"realistic: {S} samples at {fs_hz/1e6:g} MS/s, {n_codes} codes x {n_chips} chips, "
+                    f"sps {sps}, {len(freqs)} bins, {len(tags)} tags", x, chips, sps, fs_hz, freqs, N,
+                    tags, sigma)
+
+
+def small(seed: int = 11, S: int = 40000, n_codes: int = 3, n_chips: int = 600, sps: int = 4,
+          fs_hz: float = 4e6, N: int = 8192, freqs_hz: Optional[np.ndarray] = None, n_tags: int = 4,
+          snr_range=(-12.0, -3.0), sigma: float = 2048.0) -> Workload:
+    """A few ragged windows (S not a multiple of the hop), several codes, an odd
+    bin count; small enough that the oracle finishes in well under a second."""
+    freqs = freq_grid(-3000.0, 3000.0, 1500.0) if freqs_hz is None else np.asarray(freqs_hz, np.float64)
+    return realistic(seed=seed, seconds=S / fs_hz, n_codes=n_codes, n_chips=n_chips, sps=sps,
+                     fs_hz=fs_hz, n_tags=n_tags, snr_range=snr_range, freqs_hz=freqs,
+                     sigma=sigma, jitter_hz=20.0, min_same_code_gap=2 * N, fft_len=N)
