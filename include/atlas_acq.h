@@ -1,0 +1,165 @@
+/*
+ * atlas_acq.h -- C ABI of the GB300 acquisition-mode time-of-arrival search.
+ *
+ * The search (Rubinpur & Toledo, "Signal Processing for a Reverse-GPS Wildlife
+ * Tracking System", arXiv 2005.10445) detects which tag codes appear in a
+ * block of complex baseband samples and estimates a sub-sample time of
+ * arrival for each (Section 2, problem statement; Section 3, steps 1-8).
+ * This library runs the coherent form of that search over every code and a
+ * grid of carrier-frequency offsets:
+ *
+ *   for every overlapping window w (Section 2.1: blocks overlap so that each
+ *   transmission lies entirely in one block; here hop = N - L), every code c
+ *   and every frequency bin k:
+ *     y[m]      = x[w*hop + m] * exp(-j 2 pi f_k m / fs)        (Section 3 step 2,
+ *                                                                one LO mix per bin)
+ *     corr[tau] = sum_{n<L} y[(tau+n) mod N] * r_c[n]           (step 7; computed with
+ *                                                                FFTs, Section 4.1)
+ *     P = |corr|^2, floor = mean_{tau<N} P, (P*, tau*) = argmax over the window's
+ *     valid lags (smallest lag on ties)                          (step 8)
+ *   per (w, c): the bin with the largest score P_max / floor (smallest bin on
+ *   ties) is a detection when score >= threshold; its peak is then refined
+ *   ("interpolated", step 8) by recomputing |corr|^2 directly in FP64 at the
+ *   absolute lags a-1, a, a+1 and taking the vertex of the parabola.
+ *
+ * r_c[n] = chip_c[n / sps] for n < L = chips_c * sps (the replica, step 6).
+ * Samples are interleaved float32 (re, im) pairs ("complex64").
+ *
+ * Threading: a context may be used from one host thread at a time.  All
+ * device work is stream-ordered on the stream the caller passes.
+ * Errors: every call returns ATLAS_OK (0) or a negative ATLAS_ERR_* code;
+ * atlas_acq_strerror() gives a message.  After ATLAS_ERR_CUDA the CUDA error
+ * string is available from atlas_acq_last_error().
+ */
+#ifndef ATLAS_ACQ_H_
+#define ATLAS_ACQ_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ATLAS_OK = 0,
+  ATLAS_ERR_INVALID_ARG = -1,  /* null pointer, non-positive count, stream shorter than a code ... */
+  ATLAS_ERR_CUDA = -2,         /* a CUDA runtime call failed; see atlas_acq_last_error() */
+  ATLAS_ERR_NO_MEMORY = -3,    /* device or host allocation failed (create time only) */
+  ATLAS_ERR_UNSUPPORTED = -4,  /* a size outside what the kernels support (see atlas_acq_create) */
+  ATLAS_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+  ATLAS_ERR_DEVICE = -6        /* a kernel reported an internal check failure (device status word) */
+};
+
+typedef struct atlas_acq_ctx* atlas_acq_t;
+
+/* One detection (32 bytes).  Written by the library into caller-owned memory. */
+typedef struct {
+  int32_t code;       /* code index, 0 .. n_codes-1 */
+  int32_t window;     /* window index w; the window starts at sample w*hop_c */
+  int32_t lag;        /* window-relative lag tau*; absolute lag a = window*hop_c + lag */
+  int32_t freq_bin;   /* index k into the frequency grid */
+  float   score;      /* P_max / floor of the chosen (w, c, k) cell (FP32 FFT path) */
+  float   peak_power; /* |corr|^2 at absolute lag a, recomputed directly in FP64 */
+  double  toa;        /* a + delta, samples from the stream start (FP64) */
+} atlas_detection;
+
+/* Per-cell statistics (16 bytes), for inspection and testing. */
+typedef struct {
+  float   p_max;      /* P* over the window's valid lags */
+  float   floor;      /* mean of P over all N circular lags */
+  int32_t lag;        /* tau* (smallest on ties) */
+  int32_t valid;      /* 1 if this (w, c) window exists for the code, else 0 */
+} atlas_cell;
+
+typedef struct {
+  float   threshold;       /* detection threshold on P_max / floor; default 25 */
+  int32_t fft_len;         /* N for every code; 0 = 2 * nextpow2(L_c) per code */
+  int32_t windows_per_launch; /* windows processed per launch group; 0 = automatic */
+  int32_t reserved[5];
+} atlas_acq_opts;
+
+/* Fill *opts with the defaults. */
+void atlas_acq_default_opts(atlas_acq_opts* opts);
+
+/*
+ * Create a search context on the current CUDA device.
+ *   chips           host, n_codes concatenated +/-1 int8 chip sequences (copied)
+ *   chips_per_code  host, [n_codes] chip counts (each >= 1)
+ *   samples_per_chip  sps >= 1; a power of two
+ *   fs_hz           sample rate (> 0)
+ *   freq_offsets_hz host, [n_freq] carrier offsets f_k in Hz (copied)
+ *   opts            NULL for defaults
+ * Builds the stored, conjugated code spectra on the device (Section 4.2: the
+ * transformed replicas are computed once and kept), allocates every
+ * workspace the searches need (Section 4.2: preallocated, size-keyed arrays
+ * that are reused), and synchronises the device before returning.
+ * Supported sizes: N a power of two with N >= L_c, N/sps between 2^10 and
+ * 2^14; otherwise ATLAS_ERR_UNSUPPORTED.  Ownership: *out is owned by the
+ * caller and released with atlas_acq_destroy().
+ */
+int atlas_acq_create(atlas_acq_t* out, const int8_t* chips, const int32_t* chips_per_code,
+                     int32_t n_codes, int32_t samples_per_chip, double fs_hz,
+                     const double* freq_offsets_hz, int32_t n_freq, const atlas_acq_opts* opts);
+
+/* Window plan of code `code` for a stream of n_samples (pure query, no device
+ * work): W = max(1, ceil((S - N) / hop) + 1), hop = N - L (Section 2.1). */
+int atlas_acq_windows(atlas_acq_t ctx, int32_t code, int64_t n_samples, int32_t* n_windows,
+                      int32_t* hop, int32_t* fft_len);
+
+/*
+ * Run the search on a device-resident stream.
+ *   stream     cudaStream_t (as void*); NULL = the legacy default stream
+ *   d_iq       device, [n_samples][2] float32 interleaved (re, im), caller-owned
+ *   n_samples  S >= the longest code length L
+ *   d_out      device, [capacity] atlas_detection, caller-owned
+ *   capacity   >= 0
+ *   d_count    device, one int32: receives the number of detections found
+ *              (may exceed capacity; only the first `capacity` are written)
+ * Detections are ordered by (code length group, window, code) -- by (window,
+ * code) when all codes have the same length -- so repeated runs are
+ * bit-identical.  Asynchronous: results are valid after the caller
+ * synchronises `stream`.  Allocates nothing.  Returns ATLAS_ERR_INVALID_ARG
+ * for bad pointers or sizes, ATLAS_ERR_CUDA if a launch fails.
+ */
+int atlas_acq_run(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t n_samples,
+                  atlas_detection* d_out, int32_t capacity, int32_t* d_count);
+
+/*
+ * Same search with per-cell statistics: d_cells (device, caller-owned) gets
+ * [max_windows][n_codes][n_freq] atlas_cell, where max_windows is the largest
+ * W over the codes (atlas_acq_windows); cells of windows a code does not have
+ * are written with valid = 0.  d_out/d_count behave as in atlas_acq_run.
+ */
+int atlas_acq_run_cells(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t n_samples,
+                        atlas_cell* d_cells, atlas_detection* d_out, int32_t capacity,
+                        int32_t* d_count);
+
+/*
+ * End-to-end form on HOST buffers: copies h_iq to the device, runs the search
+ * and copies the count and the first min(count, capacity) detections back,
+ * then synchronises `stream`.  h_iq, h_out and h_count are host memory (pinned
+ * memory makes the copies asynchronous DMA).  The device staging buffer for
+ * the samples is allocated on first use for a given size and kept by the
+ * context (Section 4.2 memoization); *h_count receives the full count.
+ */
+int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t n_samples,
+                       atlas_detection* h_out, int32_t capacity, int32_t* h_count);
+
+/* Device status word of the last run (0 = no kernel-side check failed).
+ * Synchronises the device. */
+int atlas_acq_last_device_status(atlas_acq_t ctx);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* atlas_acq_last_error(atlas_acq_t ctx);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+void atlas_acq_destroy(atlas_acq_t ctx);
+
+/* Static message for a status code. */
+const char* atlas_acq_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATLAS_ACQ_H_ */

@@ -1,0 +1,218 @@
+"""Thin ctypes binding over ``libatlas_acq.so`` (include/atlas_acq.h).
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels.  Device buffers are passed as raw pointers (``tensor.data_ptr()``
+of torch CUDA tensors) and streams as ``torch.cuda.Stream.cuda_stream``.
+Loading fails loudly when the library has not been built; there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libatlas_acq.so")
+
+ATLAS_OK = 0
+ATLAS_ERR_INVALID_ARG = -1
+ATLAS_ERR_CUDA = -2
+ATLAS_ERR_NO_MEMORY = -3
+ATLAS_ERR_UNSUPPORTED = -4
+ATLAS_ERR_TIMEOUT = -5
+ATLAS_ERR_DEVICE = -6
+
+# Every symbol include/atlas_acq.h declares.
+EXPORTED = [
+    "atlas_acq_default_opts", "atlas_acq_create", "atlas_acq_windows", "atlas_acq_run",
+    "atlas_acq_run_cells", "atlas_acq_run_host", "atlas_acq_last_device_status",
+    "atlas_acq_last_error", "atlas_acq_destroy", "atlas_acq_strerror",
+]
+
+
+class Detection(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("window", ctypes.c_int32), ("lag", ctypes.c_int32),
+                ("freq_bin", ctypes.c_int32), ("score", ctypes.c_float), ("peak_power", ctypes.c_float),
+                ("toa", ctypes.c_double)]
+
+
+class Cell(ctypes.Structure):
+    _fields_ = [("p_max", ctypes.c_float), ("floor", ctypes.c_float), ("lag", ctypes.c_int32),
+                ("valid", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_float), ("fft_len", ctypes.c_int32),
+                ("windows_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+DETECTION_DTYPE = np.dtype([("code", "<i4"), ("window", "<i4"), ("lag", "<i4"), ("freq_bin", "<i4"),
+                            ("score", "<f4"), ("peak_power", "<f4"), ("toa", "<f8")])
+CELL_DTYPE = np.dtype([("p_max", "<f4"), ("floor", "<f4"), ("lag", "<i4"), ("valid", "<i4")])
+assert DETECTION_DTYPE.itemsize == ctypes.sizeof(Detection) == 32
+assert CELL_DTYPE.itemsize == ctypes.sizeof(Cell) == 16
+
+_lib = None
+
+
+class AtlasError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"atlas_acq error {status}: {msg}")
+        self.status = status
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load the shared library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.atlas_acq_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.atlas_acq_default_opts.restype = None
+    lib.atlas_acq_create.argtypes = [ctypes.POINTER(vp), vp, vp, i32, i32, f64, vp, i32, ctypes.POINTER(Opts)]
+    lib.atlas_acq_create.restype = ctypes.c_int
+    lib.atlas_acq_windows.argtypes = [vp, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.atlas_acq_windows.restype = ctypes.c_int
+    lib.atlas_acq_run.argtypes = [vp, vp, vp, i64, vp, i32, vp]
+    lib.atlas_acq_run.restype = ctypes.c_int
+    lib.atlas_acq_run_cells.argtypes = [vp, vp, vp, i64, vp, vp, i32, vp]
+    lib.atlas_acq_run_cells.restype = ctypes.c_int
+    lib.atlas_acq_run_host.argtypes = [vp, vp, vp, i64, vp, i32, vp]
+    lib.atlas_acq_run_host.restype = ctypes.c_int
+    lib.atlas_acq_last_device_status.argtypes = [vp]
+    lib.atlas_acq_last_device_status.restype = ctypes.c_int
+    lib.atlas_acq_last_error.argtypes = [vp]
+    lib.atlas_acq_last_error.restype = ctypes.c_char_p
+    lib.atlas_acq_destroy.argtypes = [vp]
+    lib.atlas_acq_destroy.restype = None
+    lib.atlas_acq_strerror.argtypes = [ctypes.c_int]
+    lib.atlas_acq_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    return load().atlas_acq_strerror(status).decode()
+
+
+def _check(status: int, ctx=None) -> None:
+    if status != ATLAS_OK:
+        msg = strerror(status)
+        if ctx is not None and status == ATLAS_ERR_CUDA:
+            msg += ": " + load().atlas_acq_last_error(ctx).decode()
+        raise AtlasError(status, msg)
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load().atlas_acq_default_opts(ctypes.byref(o))
+    return o
+
+
+class Search:
+    """A search context (atlas_acq_create / atlas_acq_destroy)."""
+
+    def __init__(self, chips: Sequence[np.ndarray], samples_per_chip: int, fs_hz: float,
+                 freq_offsets_hz: Sequence[float], threshold: float = 25.0, fft_len: int = 0,
+                 windows_per_launch: int = 0):
+        lib = load()
+        self._lib = lib
+        self.ctx = ctypes.c_void_p()
+        cat = np.ascontiguousarray(np.concatenate([np.asarray(c, np.int8) for c in chips]))
+        cpc = np.ascontiguousarray(np.array([len(c) for c in chips], np.int32))
+        fr = np.ascontiguousarray(np.asarray(freq_offsets_hz, np.float64))
+        o = default_opts()
+        o.threshold = threshold
+        o.fft_len = fft_len
+        o.windows_per_launch = windows_per_launch
+        self.n_codes = len(chips)
+        self.n_freq = len(fr)
+        st = lib.atlas_acq_create(ctypes.byref(self.ctx), cat.ctypes.data, cpc.ctypes.data, len(chips),
+                                  samples_per_chip, float(fs_hz), fr.ctypes.data, len(fr), ctypes.byref(o))
+        if st != ATLAS_OK:
+            self.ctx = None
+        _check(st)
+
+    def close(self) -> None:
+        if self.ctx:
+            self._lib.atlas_acq_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def windows(self, code: int, n_samples: int):
+        W, hop, N = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.atlas_acq_windows(self.ctx, code, n_samples, ctypes.byref(W), ctypes.byref(hop),
+                                           ctypes.byref(N)))
+        return W.value, hop.value, N.value
+
+    def max_windows(self, n_samples: int) -> int:
+        return max(self.windows(c, n_samples)[0] for c in range(self.n_codes))
+
+    # raw pointer forms (device memory) ------------------------------------
+    def run_ptr(self, stream: int, d_iq: int, n_samples: int, d_out: int, capacity: int, d_count: int) -> None:
+        _check(self._lib.atlas_acq_run(self.ctx, stream, d_iq, n_samples, d_out, capacity, d_count), self.ctx)
+
+    def run_cells_ptr(self, stream: int, d_iq: int, n_samples: int, d_cells: int, d_out: int, capacity: int,
+                      d_count: int) -> None:
+        _check(self._lib.atlas_acq_run_cells(self.ctx, stream, d_iq, n_samples, d_cells, d_out, capacity,
+                                             d_count), self.ctx)
+
+    def run_host_ptr(self, stream: int, h_iq: int, n_samples: int, h_out: int, capacity: int,
+                     h_count: int) -> None:
+        _check(self._lib.atlas_acq_run_host(self.ctx, stream, h_iq, n_samples, h_out, capacity, h_count),
+               self.ctx)
+
+    def device_status(self) -> int:
+        return int(self._lib.atlas_acq_last_device_status(self.ctx))
+
+    # torch conveniences ---------------------------------------------------
+    def run(self, x_iq, capacity: int = 4096, stream=None, cells: bool = False):
+        """x_iq: torch CUDA float32 tensor [S, 2] (or complex64 [S]).  Returns
+        (detections as a numpy structured array, count, cells or None)."""
+        import torch
+        if x_iq.dtype == torch.complex64:
+            x_iq = torch.view_as_real(x_iq)
+        assert x_iq.is_cuda and x_iq.dtype == torch.float32 and x_iq.is_contiguous()
+        S = x_iq.shape[0]
+        dev = x_iq.device
+        out = torch.empty(max(capacity, 1) * 32, dtype=torch.uint8, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        cell_buf = None
+        if cells:
+            nw = self.max_windows(S)
+            cell_buf = torch.empty(nw * self.n_codes * self.n_freq * 16, dtype=torch.uint8, device=dev)
+            self.run_cells_ptr(st.cuda_stream, x_iq.data_ptr(), S, cell_buf.data_ptr(), out.data_ptr(), capacity,
+                               cnt.data_ptr())
+        else:
+            self.run_ptr(st.cuda_stream, x_iq.data_ptr(), S, out.data_ptr(), capacity, cnt.data_ptr())
+        st.synchronize()
+        n = int(cnt.item())
+        dets = out.cpu().numpy().view(DETECTION_DTYPE)[: min(n, capacity)].copy()
+        cell_np = None
+        if cells:
+            cell_np = cell_buf.cpu().numpy().view(CELL_DTYPE).reshape(nw, self.n_codes, self.n_freq).copy()
+        return dets, n, cell_np
+
+    def run_host(self, x_iq: np.ndarray, capacity: int = 4096, stream: int = 0):
+        """Host numpy [S, 2] float32 (or complex64 [S]) in, host detections out."""
+        if x_iq.dtype == np.complex64:
+            x_iq = x_iq.view(np.float32).reshape(-1, 2)
+        x_iq = np.ascontiguousarray(x_iq, dtype=np.float32)
+        out = np.zeros(max(capacity, 1), DETECTION_DTYPE)
+        cnt = np.zeros(1, np.int32)
+        self.run_host_ptr(stream, x_iq.ctypes.data, x_iq.shape[0], out.ctypes.data, capacity, cnt.ctypes.data)
+        n = int(cnt[0])
+        return out[: min(n, capacity)].copy(), n

@@ -1,0 +1,91 @@
+// acq_internal.h -- parameter blocks shared by the host side of the library
+// and its kernels (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "atlas_acq.h"
+
+namespace atlas {
+
+constexpr int kMinLogM = 10;
+constexpr int kMaxLogM = 14;
+constexpr int kMaxSps = 64;
+
+// Device status word bits (the kernels OR these in; 0 = all checks passed).
+enum : int {
+  kStatusBadIndex = 1,
+};
+
+// Window FFT: one block per (rho, k, window in the launch group).
+struct WindowFftParams {
+  const float2* x;          // stream [S]
+  int64_t S;
+  int N, M, sps, hop, W;    // window length, M = N / sps, samples/chip, hop, windows of the code group
+  int w0, nw;               // first window of the launch group, windows in it
+  int K;
+  const uint64_t* inc;      // [K] phase increment per sample, turns * 2^64 (two's complement)
+  const float2* tw;         // twiddle tables for log2(M)
+  float2* G;                // out [nw][K][sps][M]
+  int* status;
+};
+
+// Per-code inverse FFT and epilogue: one block per (rho, k, window, code).
+struct CorrParams {
+  const float2* G;          // [nw][K][sps][M]
+  const float2* D;          // [Cg][M] conj(FFT_M(chips)) / M
+  const float2* tw;
+  float4* part;             // out [nw][Cg][K][sps] = {sum P, P*, tau*, 0}
+  int64_t S;
+  int N, M, sps, hop, W, L;
+  int w0, nw, K, Cg;
+  int* status;
+};
+
+// Bin selection, threshold and ordered compaction for one launch group.
+struct SelectParams {
+  const float4* part;       // [nw][Cg][K][sps]
+  const int* codes;         // [Cg] global code ids of the group
+  int Cg, C, K, sps, N, W, w0, nw;
+  float threshold;
+  atlas_detection* out;
+  int capacity;
+  int* count;               // running count (device)
+  atlas_cell* cells;        // optional [Wmax][C][K]
+};
+
+// FP64 direct recompute at a-1, a, a+1 and parabolic refinement.
+struct RefineParams {
+  const float2* x;
+  int64_t S;
+  const int8_t* chips;      // concatenated
+  const int64_t* chip_off;  // [C]
+  const int* chips_per_code;// [C]
+  const int* hop;           // [C]
+  const uint64_t* inc;      // [K]
+  int sps;
+  atlas_detection* out;
+  int capacity;
+  const int* count;
+};
+
+// Code bank: conj(FFT_M(chips zero padded)) / M per code of a group.
+struct CodeBankParams {
+  const int8_t* chips;
+  const int64_t* chip_off;  // [Cg] offsets of the group's codes
+  const int* n_chips;       // [Cg]
+  const float2* tw;
+  float2* D;                // [Cg][M]
+  int M;
+  float scale;              // 1 / M
+};
+
+cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cudaStream_t s);
+cudaError_t launch_window_fft(int logM, const WindowFftParams& p, cudaStream_t s);
+cudaError_t launch_corr(int logM, const CorrParams& p, cudaStream_t s);
+cudaError_t launch_select(const SelectParams& p, cudaStream_t s);
+cudaError_t launch_refine(const RefineParams& p, int grid, cudaStream_t s);
+cudaError_t prepare_kernels();  // raises the dynamic shared-memory limits once per process
+
+}  // namespace atlas

@@ -1,0 +1,454 @@
+// acq_kernels.cu -- the CUDA kernels of the acquisition search.
+//
+// Polyphase form of the correlation.  The replica is piecewise constant:
+// r[n] = chip[n / sps] (Section 3 step 6), so with tau = sps*q + rho and
+// B[t] = sum_{s<sps} y[(t + s) mod N] (a box sum of the mixed window),
+//
+//   corr[sps*q + rho] = sum_i chip[i] * B_rho[(q + i) mod M],  B_rho[q] = B[sps*q + rho],
+//
+// a circular correlation of length M = N / sps.  By the identity of
+// Section 4.1 it equals IFFT_M(FFT_M(B_rho) * conj(FFT_M(chip))) / M.  This is
+// the same N-point correlation, with the first stage of the N-point inverse
+// transform (the sps-point DFT across stride-M elements) hoisted out of the
+// per-code loop because the code spectrum factors into
+// (chip spectrum periodised) x (box spectrum).  Per (window, bin) there are
+// sps forward transforms of M points; per (window, code, bin) there are sps
+// inverse transforms of M points, each of which fits in one block's shared
+// memory for M <= 2^14.
+//
+// Kernels, in launch order per group of windows:
+//   k_code_bank   (create time) D_c = conj(FFT_M(chip_c)) / M
+//   k_window_fft  per (rho, k, w): mix (one LO mix per bin, Section 3 step 2),
+//                 box sum, decimate by sps, FFT_M -> G[w][k][rho]
+//   k_corr        per (rho, k, w, c): G * D_c -> IFFT_M -> |.|^2 -> sum and
+//                 argmax over the window's valid lags (Section 3 steps 7-8);
+//                 the correlation never leaves the chip
+//   k_select      per (w, c): combine the sps partial results of each bin,
+//                 score = P_max / floor, best bin, threshold, ordered compaction
+//   k_refine      per detection: FP64 direct |corr|^2 at a-1, a, a+1 and the
+//                 parabola vertex (Section 3 step 8, "interpolated")
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "acq_internal.h"
+#include "fft_block.cuh"
+
+namespace atlas {
+
+constexpr int kLogE = 5;  // 32 complex values per thread
+
+// phase (turns * 2^64) -> exp(-2 pi i turns) in FP32.  The top 32 bits give the
+// angle as a fraction of a half turn in [-1, 1).
+__device__ __forceinline__ float2 expi_neg(uint64_t ph) {
+  const float h = (float)(int32_t)(ph >> 32) * 4.656612873077392578125e-10f;  // 2^-31
+  float s, c;
+  sincospif(h, &s, &c);
+  return make_float2(c, -s);
+}
+
+template <int LOGM>
+__device__ __forceinline__ void load_tables(float2* sm_tw, const float2* tw) {
+  for (int i = threadIdx.x; i < TwTables<LOGM>::N; i += blockDim.x) sm_tw[i] = tw[i];
+}
+
+// Block-wide deterministic reduction of (sum, max, argmax) with the smallest
+// lag on ties.  Result valid in thread 0.
+__device__ __forceinline__ void better(float& best, int& bt, float p, int t) {
+  if (p > best || (p == best && t < bt)) {
+    best = p;
+    bt = t;
+  }
+}
+
+__device__ __forceinline__ void block_reduce_stats(float& sum, float& best, int& bt, float4* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, sum, o);
+    const float b2 = __shfl_down_sync(0xffffffffu, best, o);
+    const int t2 = __shfl_down_sync(0xffffffffu, bt, o);
+    sum += s2;
+    better(best, bt, b2, t2);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = make_float4(sum, best, __int_as_float(bt), 0.f);
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    float4 r = lane < nw ? red[lane] : make_float4(0.f, -1.f, __int_as_float(0x7fffffff), 0.f);
+    sum = r.x;
+    best = r.y;
+    bt = __float_as_int(r.z);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_down_sync(0xffffffffu, sum, o);
+      const float b2 = __shfl_down_sync(0xffffffffu, best, o);
+      const int t2 = __shfl_down_sync(0xffffffffu, bt, o);
+      sum += s2;
+      better(best, bt, b2, t2);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// code bank (create time)
+// ---------------------------------------------------------------------------
+
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_code_bank(CodeBankParams p) {
+  using FFT = BlockFFT<LOGM, kLogE, -1>;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  load_tables<LOGM>(sm_tw, p.tw);
+  __syncthreads();
+  const int c = blockIdx.x;
+  const int8_t* ch = p.chips + p.chip_off[c];
+  const int nc = p.n_chips[c];
+  float2* D = p.D + (int64_t)c * FFT::M;
+  auto load = [&](int i) { return make_float2(i < nc ? (float)ch[i] : 0.f, 0.f); };
+  const float sc = p.scale;
+  auto emit = [&](int k, float2 v) { D[k] = make_float2(v.x * sc, -v.y * sc); };
+  FFT::run(sm, sm_tw, load, emit);
+}
+
+// ---------------------------------------------------------------------------
+// window FFT: mix + box sum + decimate + FFT_M
+// ---------------------------------------------------------------------------
+
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_window_fft(WindowFftParams p) {
+  using FFT = BlockFFT<LOGM, kLogE, -1>;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  float2* sm_in = sm_tw + TwTables<LOGM>::N;  // [sps] inner phases, then the wrap factor
+
+  const int rho = blockIdx.x, k = blockIdx.y, wl = blockIdx.z;
+  const int w = p.w0 + wl;
+  const int sps = p.sps;
+  const uint64_t inc = p.inc[k];
+  load_tables<LOGM>(sm_tw, p.tw);
+  for (int s = threadIdx.x; s < sps; s += blockDim.x) sm_in[s] = expi_neg(inc * (uint64_t)(rho + s));
+  if (threadIdx.x == 0) sm_in[sps] = expi_neg((uint64_t)0 - inc * (uint64_t)p.N);  // exp(+2 pi i f N / fs)
+  __syncthreads();
+
+  const float2* x = p.x;
+  const int64_t base = (int64_t)w * p.hop;
+  const int64_t S = p.S;
+  const int N = p.N;
+  const uint64_t inc_q = inc * (uint64_t)sps;
+  // B_rho[q] = exp(-2 pi i f sps q / fs) * sum_s x_w[sps q + rho + s] exp(-2 pi i f (rho + s) / fs),
+  // with window-relative indices taken mod N (the last q wraps to the window start).
+  auto load = [&](int q) {
+    float2 acc = make_float2(0.f, 0.f);
+    const int m0 = q * sps + rho;
+    for (int s = 0; s < sps; ++s) {
+      int m = m0 + s;
+      float2 wv = sm_in[s];
+      if (m >= N) {
+        m -= N;
+        wv = cmul(wv, sm_in[sps]);
+      }
+      const int64_t idx = base + m;
+      if (idx < S) acc = cadd(acc, cmul(x[idx], wv));
+    }
+    return cmul(acc, expi_neg(inc_q * (uint64_t)q));
+  };
+  float2* G = p.G + (((int64_t)wl * p.K + k) * sps + rho) * FFT::M;
+  auto emit = [&](int i, float2 v) { G[i] = v; };
+  FFT::run(sm, sm_tw, load, emit);
+}
+
+// ---------------------------------------------------------------------------
+// per-code correlation: G * D -> IFFT -> |.|^2 -> floor sum, argmax
+// ---------------------------------------------------------------------------
+
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_corr(CorrParams p) {
+  using FFT = BlockFFT<LOGM, kLogE, +1>;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N);
+
+  const int rho = blockIdx.x, k = blockIdx.y;
+  const int wl = blockIdx.z / p.Cg, c = blockIdx.z % p.Cg;
+  const int w = p.w0 + wl;
+  const int sps = p.sps;
+  load_tables<LOGM>(sm_tw, p.tw);
+  __syncthreads();
+
+  // valid lags of this window (Section 2.1 overlap rule): [0, hop) before the
+  // last window, [0, min(hop, S - L - w*hop)] in the last.
+  int nvalid = p.hop;
+  if (w == p.W - 1) {
+    const int64_t lim = p.S - p.L - (int64_t)w * p.hop;
+    nvalid = (int)(lim < p.hop ? lim : p.hop) + 1;
+  }
+
+  const float2* G = p.G + (((int64_t)wl * p.K + k) * sps + rho) * FFT::M;
+  const float2* D = p.D + (int64_t)c * FFT::M;
+  auto load = [&](int i) { return cmul(G[i], D[i]); };
+  float sum = 0.f, best = -1.f;
+  int bt = 0x7fffffff;
+  auto emit = [&](int q, float2 v) {
+    const float P = fmaf(v.x, v.x, v.y * v.y);
+    sum += P;
+    const int tau = q * sps + rho;
+    if (tau < nvalid) better(best, bt, P, tau);
+  };
+  FFT::run(sm, sm_tw, load, emit);
+  block_reduce_stats(sum, best, bt, red);
+  if (threadIdx.x == 0) {
+    p.part[(((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho] = make_float4(sum, best, __int_as_float(bt), 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// selection and ordered compaction (one block per launch group)
+// ---------------------------------------------------------------------------
+
+constexpr int kSelectThreads = 256;
+
+__global__ void __launch_bounds__(kSelectThreads) k_select(SelectParams p) {
+  __shared__ int scan[kSelectThreads];
+  __shared__ int base_sh;
+  if (threadIdx.x == 0) base_sh = *p.count;
+  __syncthreads();
+  const int n_pairs = p.nw * p.Cg;
+  for (int p0 = 0; p0 < n_pairs; p0 += kSelectThreads) {
+    const int pi = p0 + threadIdx.x;
+    int flag = 0, wl = 0, c = 0, bk = 0, btau = 0;
+    float bscore = -1.f, bpmax = 0.f;
+    if (pi < n_pairs) {
+      wl = pi / p.Cg;
+      c = pi % p.Cg;
+      const int w = p.w0 + wl;
+      for (int k = 0; k < p.K; ++k) {
+        const float4* pr = p.part + (((int64_t)wl * p.Cg + c) * p.K + k) * p.sps;
+        float sum = 0.f, best = -1.f;
+        int bt = 0x7fffffff;
+        for (int r = 0; r < p.sps; ++r) {
+          const float4 v = pr[r];
+          sum += v.x;
+          better(best, bt, v.y, __float_as_int(v.z));
+        }
+        const float floor_ = sum / (float)p.N;
+        const float score = floor_ > 0.f ? best / floor_ : 0.f;
+        if (p.cells) {
+          atlas_cell cell;
+          cell.p_max = best;
+          cell.floor = floor_;
+          cell.lag = bt;
+          cell.valid = 1;
+          p.cells[((int64_t)w * p.C + p.codes[c]) * p.K + k] = cell;
+        }
+        if (score > bscore) {
+          bscore = score;
+          bk = k;
+          btau = bt;
+          bpmax = best;
+        }
+      }
+      flag = bscore >= p.threshold ? 1 : 0;
+    }
+    // inclusive scan of the flags (Hillis-Steele in shared memory)
+    scan[threadIdx.x] = flag;
+    __syncthreads();
+    for (int o = 1; o < kSelectThreads; o <<= 1) {
+      const int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+      __syncthreads();
+      scan[threadIdx.x] += v;
+      __syncthreads();
+    }
+    if (flag) {
+      const int pos = base_sh + scan[threadIdx.x] - 1;
+      if (pos < p.capacity) {
+        atlas_detection d;
+        d.code = p.codes[c];
+        d.window = p.w0 + wl;
+        d.lag = btau;
+        d.freq_bin = bk;
+        d.score = bscore;
+        d.peak_power = bpmax;
+        d.toa = 0.0;
+        p.out[pos] = d;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base_sh += scan[kSelectThreads - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *p.count = base_sh;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 refinement
+// ---------------------------------------------------------------------------
+
+constexpr int kRefineThreads = 256;
+
+__device__ __forceinline__ void dadd_shfl(double& v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+}
+
+__global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams p) {
+  __shared__ double red[6][kRefineThreads / 32];
+  const int n = min(*p.count, p.capacity);
+  for (int di = blockIdx.x; di < n; di += gridDim.x) {
+    atlas_detection det = p.out[di];
+    const int c = det.code;
+    const int sps = p.sps;
+    const int L = p.chips_per_code[c] * sps;
+    const int8_t* ch = p.chips + p.chip_off[c];
+    const int64_t a = (int64_t)det.window * p.hop[c] + det.lag;
+    const uint64_t inc = p.inc[det.freq_bin];
+    // m runs over [a-1, a+L]; thread t takes m = a - 1 + t + kRefineThreads*i.
+    const int64_t m0 = a - 1 + threadIdx.x;
+    const uint64_t step_ph = inc * (uint64_t)kRefineThreads;
+    double sr, cr;
+    sincospi(2.0 * (double)(int64_t)step_ph * 5.42101086242752217e-20, &sr, &cr);  // 2^-64
+    const double str = cr, sti = -sr;  // exp(-2 pi i f * 256 / fs)
+    double s0, c0;
+    sincospi(2.0 * (double)(int64_t)(inc * (uint64_t)m0) * 5.42101086242752217e-20, &s0, &c0);
+    double er = c0, ei = -s0;  // exp(-2 pi i f m / fs)
+    double acc[6] = {0, 0, 0, 0, 0, 0};  // re/im for d = -1, 0, +1
+    int it = 0;
+    for (int64_t m = m0; m <= a + L; m += kRefineThreads, ++it) {
+      if ((it & 15) == 15) {  // re-anchor the rotation every 16 steps
+        sincospi(2.0 * (double)(int64_t)(inc * (uint64_t)m) * 5.42101086242752217e-20, &s0, &c0);
+        er = c0;
+        ei = -s0;
+      }
+      double xr = 0.0, xi = 0.0;
+      if (m >= 0 && m < p.S) {
+        const float2 xv = p.x[m];
+        xr = xv.x;
+        xi = xv.y;
+      }
+      const double yr = xr * er - xi * ei, yi = xr * ei + xi * er;
+#pragma unroll
+      for (int d = -1; d <= 1; ++d) {
+        const int64_t nn = m - a - d;
+        if (nn >= 0 && nn < L) {
+          const double rv = (double)ch[nn / sps];
+          acc[2 * (d + 1)] += yr * rv;
+          acc[2 * (d + 1) + 1] += yi * rv;
+        }
+      }
+      const double nr = er * str - ei * sti, ni = er * sti + ei * str;
+      er = nr;
+      ei = ni;
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) dadd_shfl(acc[j]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) red[j][warp] = acc[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s[6];
+      for (int j = 0; j < 6; ++j) {
+        double v = 0.0;
+        for (int q = 0; q < kRefineThreads / 32; ++q) v += red[j][q];
+        s[j] = v;
+      }
+      const double pm = s[0] * s[0] + s[1] * s[1];
+      const double p0 = s[2] * s[2] + s[3] * s[3];
+      const double pp = s[4] * s[4] + s[5] * s[5];
+      double delta = 0.0;
+      if (a - 1 >= 0 && a + 1 <= p.S - L) {
+        const double den = pm - 2.0 * p0 + pp;
+        if (den < 0.0) {
+          delta = 0.5 * (pm - pp) / den;
+          delta = delta > 0.5 ? 0.5 : (delta < -0.5 ? -0.5 : delta);
+        }
+      }
+      p.out[di].toa = (double)a + delta;
+      p.out[di].peak_power = (float)p0;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+
+template <int LOGM>
+constexpr int fft_threads() { return (1 << LOGM) >> kLogE; }
+template <int LOGM>
+constexpr size_t fft_smem() {
+  return sizeof(float2) * (BlockFFT<LOGM, kLogE, -1>::SMEM_ELEMS + TwTables<LOGM>::N) + 16 * sizeof(float4) +
+         sizeof(float2) * (kMaxSps + 1);
+}
+
+template <int LOGM>
+static cudaError_t prepare_one() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_code_bank<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fft_smem<LOGM>())) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_window_fft<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fft_smem<LOGM>())) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_corr<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGM>());
+}
+
+cudaError_t prepare_kernels() {
+  cudaError_t e;
+  if ((e = prepare_one<10>()) != cudaSuccess) return e;
+  if ((e = prepare_one<11>()) != cudaSuccess) return e;
+  if ((e = prepare_one<12>()) != cudaSuccess) return e;
+  if ((e = prepare_one<13>()) != cudaSuccess) return e;
+  return prepare_one<14>();
+}
+
+#define ATLAS_DISPATCH_LOGM(logM, CALL) \
+  switch (logM) {                       \
+    case 10: CALL(10); break;           \
+    case 11: CALL(11); break;           \
+    case 12: CALL(12); break;           \
+    case 13: CALL(13); break;           \
+    case 14: CALL(14); break;           \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cudaStream_t s) {
+#define CALL(LM) k_code_bank<LM><<<n_codes, fft_threads<LM>(), fft_smem<LM>(), s>>>(p)
+  ATLAS_DISPATCH_LOGM(logM, CALL)
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_fft(int logM, const WindowFftParams& p, cudaStream_t s) {
+  dim3 grid(p.sps, p.K, p.nw);
+#define CALL(LM) k_window_fft<LM><<<grid, fft_threads<LM>(), fft_smem<LM>(), s>>>(p)
+  ATLAS_DISPATCH_LOGM(logM, CALL)
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr(int logM, const CorrParams& p, cudaStream_t s) {
+  dim3 grid(p.sps, p.K, p.nw * p.Cg);
+#define CALL(LM) k_corr<LM><<<grid, fft_threads<LM>(), fft_smem<LM>(), s>>>(p)
+  ATLAS_DISPATCH_LOGM(logM, CALL)
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select(const SelectParams& p, cudaStream_t s) {
+  k_select<<<1, kSelectThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const RefineParams& p, int grid, cudaStream_t s) {
+  k_refine<<<grid, kRefineThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace atlas

@@ -1,0 +1,490 @@
+// atlas_acq_host.cu -- host side of the C ABI declared in include/atlas_acq.h:
+// context creation (code bank, workspaces, twiddle tables), argument
+// validation, and the stream-ordered launch sequence of a search.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "acq_internal.h"
+#include "atlas_acq.h"
+
+using atlas::CodeBankParams;
+using atlas::CorrParams;
+using atlas::RefineParams;
+using atlas::SelectParams;
+using atlas::WindowFftParams;
+
+namespace {
+
+// Codes of one length share windows (hop = N - L) and therefore the window
+// spectra; each such group is searched by one launch sequence.
+struct Group {
+  int n_chips = 0, L = 0, N = 0, M = 0, logM = 0, hop = 0;
+  std::vector<int> codes;      // global code ids
+  int* d_codes = nullptr;      // [Cg]
+  float2* d_spec = nullptr;    // [Cg][M] conj(FFT_M(chips)) / M
+  const float2* d_tw = nullptr;
+  int windows(int64_t S) const {
+    if (S <= N) return 1;
+    return (int)((S - N + hop - 1) / hop) + 1;
+  }
+};
+
+}  // namespace
+
+struct atlas_acq_ctx {
+  int device = 0;
+  int C = 0, K = 0, sps = 0;
+  double fs = 0.0;
+  float threshold = 25.f;
+  int max_L = 0;
+  int windows_per_launch = 0;
+  std::vector<int> n_chips;
+  std::vector<double> freqs;
+  std::vector<Group> groups;
+  std::vector<int> code_group;  // code -> group index
+  // device resources
+  int8_t* d_chips = nullptr;
+  int64_t* d_chip_off = nullptr;
+  int* d_n_chips = nullptr;
+  int* d_hop = nullptr;
+  uint64_t* d_inc = nullptr;
+  std::map<int, float2*> d_tw;  // logM -> twiddle tables
+  float2* d_G = nullptr;
+  size_t G_elems = 0;
+  float4* d_part = nullptr;
+  size_t part_elems = 0;
+  int* d_status = nullptr;
+  int wc_max = 1;  // windows per launch group (sizes the workspaces)
+  // host-buffer path (allocated on first use per size, kept)
+  float2* d_stage = nullptr;
+  int64_t stage_samples = 0;
+  atlas_detection* d_stage_out = nullptr;
+  int stage_cap = 0;
+  int* d_stage_count = nullptr;
+  std::string last_error;
+};
+
+namespace {
+
+int fail_cuda(atlas_acq_ctx* ctx, cudaError_t e) {
+  if (ctx) ctx->last_error = cudaGetErrorString(e);
+  return ATLAS_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return fail_cuda(ctx, e_); \
+  } while (0)
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int64_t v) {
+  int r = 0;
+  while ((1ll << r) < v) ++r;
+  return r;
+}
+
+// turns * 2^64 of f/fs, reduced to [-1/2, 1/2) turns, as two's complement.
+uint64_t phase_increment(double f_hz, double fs_hz) {
+  double t = f_hz / fs_hz;
+  t -= nearbyint(t);
+  if (t >= 0.5) t -= 1.0;
+  const double scaled = ldexp(t, 64);
+  return (uint64_t)(int64_t)llrint(scaled);
+}
+
+// W_M^t = exp(-2 pi i t / M): HI[i] = W^{i << LB}, LO[i] = W^i, FP64 then rounded.
+std::vector<float2> twiddle_tables(int logM) {
+  const int LB = logM / 2, HB = logM - LB;
+  const int nlo = 1 << LB, nhi = 1 << HB;
+  const double M = (double)(1 << logM);
+  std::vector<float2> t(nlo + nhi);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int i = 0; i < nhi; ++i) {
+    const double a = -two_pi * (double)((int64_t)i << LB) / M;
+    t[i] = make_float2((float)cos(a), (float)sin(a));
+  }
+  for (int i = 0; i < nlo; ++i) {
+    const double a = -two_pi * (double)i / M;
+    t[nhi + i] = make_float2((float)cos(a), (float)sin(a));
+  }
+  return t;
+}
+
+void free_ctx(atlas_acq_ctx* ctx) {
+  if (!ctx) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  for (auto& g : ctx->groups) {
+    cudaFree(g.d_codes);
+    cudaFree(g.d_spec);
+  }
+  for (auto& kv : ctx->d_tw) cudaFree(kv.second);
+  cudaFree(ctx->d_chips);
+  cudaFree(ctx->d_chip_off);
+  cudaFree(ctx->d_n_chips);
+  cudaFree(ctx->d_hop);
+  cudaFree(ctx->d_inc);
+  cudaFree(ctx->d_G);
+  cudaFree(ctx->d_part);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_stage_out);
+  cudaFree(ctx->d_stage_count);
+  cudaSetDevice(prev);
+  delete ctx;
+}
+
+template <class T>
+cudaError_t upload(T** dptr, const T* h, size_t n) {
+  cudaError_t e = cudaMalloc((void**)dptr, sizeof(T) * (n ? n : 1));
+  if (e != cudaSuccess) return e;
+  if (n) e = cudaMemcpy(*dptr, h, sizeof(T) * n, cudaMemcpyHostToDevice);
+  return e;
+}
+
+int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_per_code, int32_t n_codes,
+                int32_t sps, double fs_hz, const double* freqs, int32_t n_freq, const atlas_acq_opts& o) {
+  ctx->C = n_codes;
+  ctx->K = n_freq;
+  ctx->sps = sps;
+  ctx->fs = fs_hz;
+  ctx->threshold = o.threshold;
+  ctx->windows_per_launch = o.windows_per_launch;
+  ctx->freqs.assign(freqs, freqs + n_freq);
+  ctx->n_chips.assign(chips_per_code, chips_per_code + n_codes);
+
+  // groups by code length
+  std::map<int, int> by_len;
+  std::vector<int64_t> off(n_codes);
+  int64_t total = 0;
+  ctx->code_group.resize(n_codes);
+  for (int c = 0; c < n_codes; ++c) {
+    off[c] = total;
+    total += chips_per_code[c];
+    const int nc = chips_per_code[c];
+    auto it = by_len.find(nc);
+    if (it == by_len.end()) {
+      Group g;
+      g.n_chips = nc;
+      g.L = nc * sps;
+      g.N = o.fft_len ? o.fft_len : 2 * (int)(1ll << ilog2(g.L));
+      if (!is_pow2(g.N) || g.N <= g.L) return o.fft_len ? ATLAS_ERR_UNSUPPORTED : ATLAS_ERR_INVALID_ARG;
+      g.M = g.N / sps;
+      g.logM = ilog2(g.M);
+      if (g.logM < atlas::kMinLogM || g.logM > atlas::kMaxLogM) return ATLAS_ERR_UNSUPPORTED;
+      g.hop = g.N - g.L;
+      by_len[nc] = (int)ctx->groups.size();
+      ctx->groups.push_back(g);
+      it = by_len.find(nc);
+    }
+    ctx->code_group[c] = it->second;
+    ctx->groups[it->second].codes.push_back(c);
+    ctx->max_L = std::max(ctx->max_L, nc * sps);
+  }
+  for (int64_t i = 0; i < total; ++i)
+    if (chips[i] != 1 && chips[i] != -1) return ATLAS_ERR_INVALID_ARG;
+
+  CK(cudaGetDevice(&ctx->device));
+  CK(atlas::prepare_kernels());
+  CK(upload(&ctx->d_chips, chips, (size_t)total));
+  CK(upload(&ctx->d_chip_off, off.data(), off.size()));
+  CK(upload(&ctx->d_n_chips, chips_per_code, (size_t)n_codes));
+  std::vector<int> hops(n_codes);
+  for (int c = 0; c < n_codes; ++c) hops[c] = ctx->groups[ctx->code_group[c]].hop;
+  CK(upload(&ctx->d_hop, hops.data(), hops.size()));
+  std::vector<uint64_t> inc(n_freq);
+  for (int k = 0; k < n_freq; ++k) inc[k] = phase_increment(freqs[k], fs_hz);
+  CK(upload(&ctx->d_inc, inc.data(), inc.size()));
+  CK(cudaMalloc((void**)&ctx->d_status, sizeof(int)));
+  CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+
+  // windows per launch group: keep the window spectra of one group near L2 size
+  const size_t budget = 64ull << 20;
+  size_t max_win_bytes = 0;
+  size_t max_part_per_win = 0;
+  for (auto& g : ctx->groups) {
+    max_win_bytes = std::max(max_win_bytes, (size_t)n_freq * g.N * sizeof(float2));
+    max_part_per_win = std::max(max_part_per_win, (size_t)g.codes.size() * n_freq * sps);
+  }
+  int wc = o.windows_per_launch > 0 ? o.windows_per_launch : (int)std::max<size_t>(1, budget / max_win_bytes);
+  wc = std::min(wc, 64);
+  ctx->wc_max = wc;
+  ctx->G_elems = (size_t)wc * max_win_bytes / sizeof(float2);
+  ctx->part_elems = (size_t)wc * max_part_per_win;
+  if (cudaMalloc((void**)&ctx->d_G, ctx->G_elems * sizeof(float2)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
+  if (cudaMalloc((void**)&ctx->d_part, ctx->part_elems * sizeof(float4)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
+
+  // twiddle tables and code banks
+  for (auto& g : ctx->groups) {
+    if (!ctx->d_tw.count(g.logM)) {
+      std::vector<float2> t = twiddle_tables(g.logM);
+      float2* d = nullptr;
+      CK(upload(&d, t.data(), t.size()));
+      ctx->d_tw[g.logM] = d;
+    }
+    g.d_tw = ctx->d_tw[g.logM];
+    CK(upload(&g.d_codes, g.codes.data(), g.codes.size()));
+    if (cudaMalloc((void**)&g.d_spec, sizeof(float2) * (size_t)g.M * g.codes.size()) != cudaSuccess)
+      return ATLAS_ERR_NO_MEMORY;
+    std::vector<int64_t> goff(g.codes.size());
+    std::vector<int> gn(g.codes.size());
+    for (size_t i = 0; i < g.codes.size(); ++i) {
+      goff[i] = off[g.codes[i]];
+      gn[i] = chips_per_code[g.codes[i]];
+    }
+    int64_t* d_goff = nullptr;
+    int* d_gn = nullptr;
+    CK(upload(&d_goff, goff.data(), goff.size()));
+    CK(upload(&d_gn, gn.data(), gn.size()));
+    CodeBankParams p;
+    p.chips = ctx->d_chips;
+    p.chip_off = d_goff;
+    p.n_chips = d_gn;
+    p.tw = g.d_tw;
+    p.D = g.d_spec;
+    p.M = g.M;
+    p.scale = 1.0f / (float)g.M;
+    cudaError_t e = atlas::launch_code_bank(g.logM, p, (int)g.codes.size(), 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_goff);
+    cudaFree(d_gn);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+  }
+  return ATLAS_OK;
+}
+
+int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, atlas_cell* cells,
+             atlas_detection* out, int capacity, int* d_count) {
+  CK(cudaMemsetAsync(d_count, 0, sizeof(int), st));
+  if (cells) {
+    int wmax = 0;
+    for (auto& g : ctx->groups) wmax = std::max(wmax, g.windows(S));
+    CK(cudaMemsetAsync(cells, 0, sizeof(atlas_cell) * (size_t)wmax * ctx->C * ctx->K, st));
+  }
+  for (auto& g : ctx->groups) {
+    const int W = g.windows(S);
+    const int Cg = (int)g.codes.size();
+    const int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
+    for (int w0 = 0; w0 < W; w0 += wc) {
+      const int nw = std::min(wc, W - w0);
+      WindowFftParams a;
+      a.x = x;
+      a.S = S;
+      a.N = g.N;
+      a.M = g.M;
+      a.sps = ctx->sps;
+      a.hop = g.hop;
+      a.W = W;
+      a.w0 = w0;
+      a.nw = nw;
+      a.K = ctx->K;
+      a.inc = ctx->d_inc;
+      a.tw = g.d_tw;
+      a.G = ctx->d_G;
+      a.status = ctx->d_status;
+      CK(atlas::launch_window_fft(g.logM, a, st));
+      CorrParams b;
+      b.G = ctx->d_G;
+      b.D = g.d_spec;
+      b.tw = g.d_tw;
+      b.part = ctx->d_part;
+      b.S = S;
+      b.N = g.N;
+      b.M = g.M;
+      b.sps = ctx->sps;
+      b.hop = g.hop;
+      b.W = W;
+      b.L = g.L;
+      b.w0 = w0;
+      b.nw = nw;
+      b.K = ctx->K;
+      b.Cg = Cg;
+      b.status = ctx->d_status;
+      CK(atlas::launch_corr(g.logM, b, st));
+      SelectParams c;
+      c.part = ctx->d_part;
+      c.codes = g.d_codes;
+      c.Cg = Cg;
+      c.C = ctx->C;
+      c.K = ctx->K;
+      c.sps = ctx->sps;
+      c.N = g.N;
+      c.W = W;
+      c.w0 = w0;
+      c.nw = nw;
+      c.threshold = ctx->threshold;
+      c.out = out;
+      c.capacity = capacity;
+      c.count = d_count;
+      c.cells = cells;
+      CK(atlas::launch_select(c, st));
+    }
+  }
+  if (capacity > 0) {
+    RefineParams r;
+    r.x = x;
+    r.S = S;
+    r.chips = ctx->d_chips;
+    r.chip_off = ctx->d_chip_off;
+    r.chips_per_code = ctx->d_n_chips;
+    r.hop = ctx->d_hop;
+    r.inc = ctx->d_inc;
+    r.sps = ctx->sps;
+    r.out = out;
+    r.capacity = capacity;
+    r.count = d_count;
+    CK(atlas::launch_refine(r, std::min(capacity, 1024), st));
+  }
+  return ATLAS_OK;
+}
+
+int check_run_args(atlas_acq_ctx* ctx, const void* x, int64_t S, const void* out, int capacity,
+                   const void* count) {
+  if (!ctx || !x || !count || capacity < 0 || (capacity > 0 && !out)) return ATLAS_ERR_INVALID_ARG;
+  if (S < ctx->max_L || S > (int64_t)INT32_MAX * 8) return ATLAS_ERR_INVALID_ARG;
+  return ATLAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void atlas_acq_default_opts(atlas_acq_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->threshold = 25.f;
+  o->fft_len = 0;
+  o->windows_per_launch = 0;
+}
+
+int atlas_acq_create(atlas_acq_t* out, const int8_t* chips, const int32_t* chips_per_code, int32_t n_codes,
+                     int32_t samples_per_chip, double fs_hz, const double* freq_offsets_hz, int32_t n_freq,
+                     const atlas_acq_opts* opts) {
+  if (!out) return ATLAS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!chips || !chips_per_code || n_codes <= 0 || samples_per_chip <= 0 || !(fs_hz > 0.0) ||
+      !freq_offsets_hz || n_freq <= 0)
+    return ATLAS_ERR_INVALID_ARG;
+  if (!is_pow2(samples_per_chip) || samples_per_chip > atlas::kMaxSps) return ATLAS_ERR_UNSUPPORTED;
+  for (int c = 0; c < n_codes; ++c)
+    if (chips_per_code[c] <= 0) return ATLAS_ERR_INVALID_ARG;
+  for (int k = 0; k < n_freq; ++k)
+    if (!isfinite(freq_offsets_hz[k])) return ATLAS_ERR_INVALID_ARG;
+  atlas_acq_opts o;
+  atlas_acq_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.threshold >= 0.f) || o.fft_len < 0 || o.windows_per_launch < 0) return ATLAS_ERR_INVALID_ARG;
+  atlas_acq_ctx* ctx = new (std::nothrow) atlas_acq_ctx();
+  if (!ctx) return ATLAS_ERR_NO_MEMORY;
+  const int st = create_impl(ctx, chips, chips_per_code, n_codes, samples_per_chip, fs_hz, freq_offsets_hz,
+                             n_freq, o);
+  if (st != ATLAS_OK) {
+    free_ctx(ctx);
+    return st;
+  }
+  *out = ctx;
+  return ATLAS_OK;
+}
+
+int atlas_acq_windows(atlas_acq_t ctx, int32_t code, int64_t n_samples, int32_t* n_windows, int32_t* hop,
+                      int32_t* fft_len) {
+  if (!ctx || code < 0 || code >= ctx->C || n_samples < ctx->max_L) return ATLAS_ERR_INVALID_ARG;
+  const Group& g = ctx->groups[ctx->code_group[code]];
+  if (n_windows) *n_windows = g.windows(n_samples);
+  if (hop) *hop = g.hop;
+  if (fft_len) *fft_len = g.N;
+  return ATLAS_OK;
+}
+
+int atlas_acq_run(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t n_samples, atlas_detection* d_out,
+                  int32_t capacity, int32_t* d_count) {
+  const int a = check_run_args(ctx, d_iq, n_samples, d_out, capacity, d_count);
+  if (a != ATLAS_OK) return a;
+  return run_impl(ctx, (cudaStream_t)stream, reinterpret_cast<const float2*>(d_iq), n_samples, nullptr, d_out,
+                  capacity, d_count);
+}
+
+int atlas_acq_run_cells(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t n_samples, atlas_cell* d_cells,
+                        atlas_detection* d_out, int32_t capacity, int32_t* d_count) {
+  const int a = check_run_args(ctx, d_iq, n_samples, d_out, capacity, d_count);
+  if (a != ATLAS_OK) return a;
+  if (!d_cells) return ATLAS_ERR_INVALID_ARG;
+  return run_impl(ctx, (cudaStream_t)stream, reinterpret_cast<const float2*>(d_iq), n_samples, d_cells, d_out,
+                  capacity, d_count);
+}
+
+int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t n_samples, atlas_detection* h_out,
+                       int32_t capacity, int32_t* h_count) {
+  const int a = check_run_args(ctx, h_iq, n_samples, h_out, capacity, h_count);
+  if (a != ATLAS_OK) return a;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->stage_samples < n_samples) {
+    CK(cudaFree(ctx->d_stage));
+    ctx->d_stage = nullptr;
+    ctx->stage_samples = 0;
+    if (cudaMalloc((void**)&ctx->d_stage, sizeof(float2) * (size_t)n_samples) != cudaSuccess)
+      return ATLAS_ERR_NO_MEMORY;
+    ctx->stage_samples = n_samples;
+  }
+  if (ctx->stage_cap < std::max(capacity, 1)) {
+    CK(cudaFree(ctx->d_stage_out));
+    ctx->d_stage_out = nullptr;
+    ctx->stage_cap = 0;
+    if (cudaMalloc((void**)&ctx->d_stage_out, sizeof(atlas_detection) * (size_t)std::max(capacity, 1)) !=
+        cudaSuccess)
+      return ATLAS_ERR_NO_MEMORY;
+    ctx->stage_cap = std::max(capacity, 1);
+  }
+  if (!ctx->d_stage_count) {
+    if (cudaMalloc((void**)&ctx->d_stage_count, sizeof(int)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
+  }
+  CK(cudaMemcpyAsync(ctx->d_stage, h_iq, sizeof(float2) * (size_t)n_samples, cudaMemcpyHostToDevice, st));
+  const int r = run_impl(ctx, st, ctx->d_stage, n_samples, nullptr, ctx->d_stage_out, capacity, ctx->d_stage_count);
+  if (r != ATLAS_OK) return r;
+  CK(cudaMemcpyAsync(h_count, ctx->d_stage_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int n = std::min(*h_count, capacity);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(h_out, ctx->d_stage_out, sizeof(atlas_detection) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return ATLAS_OK;
+}
+
+int atlas_acq_last_device_status(atlas_acq_t ctx) {
+  if (!ctx) return ATLAS_ERR_INVALID_ARG;
+  int v = 0;
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  return v;
+}
+
+const char* atlas_acq_last_error(atlas_acq_t ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+void atlas_acq_destroy(atlas_acq_t ctx) { free_ctx(ctx); }
+
+const char* atlas_acq_strerror(int status) {
+  switch (status) {
+    case ATLAS_OK: return "ok";
+    case ATLAS_ERR_INVALID_ARG: return "invalid argument";
+    case ATLAS_ERR_CUDA: return "CUDA runtime error";
+    case ATLAS_ERR_NO_MEMORY: return "out of memory";
+    case ATLAS_ERR_UNSUPPORTED: return "unsupported size";
+    case ATLAS_ERR_TIMEOUT: return "device wait timed out";
+    case ATLAS_ERR_DEVICE: return "device-side check failed";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// fft_block.cuh -- one complex FFT of M = 2^LOGM points per thread block,
+// held in shared memory, for the on-chip correlation (Section 4.1 computes
+// cross-correlations with FFTs; here every transform stays on chip).
+//
+// Structure: self-sorting Stockham passes.  Pass p has radix R = 2^RB and
+// follows passes whose radices multiply to Ns = 2^D.  Sub-transform j reads
+// the R values j + r*M/R, multiplies value r by W_{Ns*R}^{(j mod Ns)*r}, does
+// an R-point DFT in registers and writes value r to
+// (j / Ns)*Ns*R + (j mod Ns) + r*Ns.  Outputs end in natural order, so no
+// bit reversal pass is needed.  The first pass takes its inputs from a
+// caller functor (global loads fused with the preceding elementwise work) and
+// the last pass hands its outputs to a caller functor (fused epilogue), so a
+// transform costs (passes - 1) round trips through shared memory.
+//
+// Every thread owns E = 2^LOGE values (T = M / E threads).  Shared memory is
+// padded by one element per 32 (index i lives at i + i/32) so that the strided
+// writes of the first pass are free of bank conflicts.
+//
+// Twiddles W_M^t come from two small tables, W_M^t = HI[t >> LB] * LO[t & (2^LB - 1)],
+// each entry the correctly rounded FP32 value of a FP64 evaluation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <utility>
+
+namespace atlas {
+
+// ---------------------------------------------------------------------------
+// compile-time constants
+// ---------------------------------------------------------------------------
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+constexpr int ct_log2(int x) { return x <= 1 ? 0 : 1 + ct_log2(x >> 1); }
+
+constexpr int ct_brev(int x, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r = (r << 1) | ((x >> i) & 1);
+  return r;
+}
+
+// sin / cos of x in [-2 pi, 2 pi] by their Maclaurin series (compile time only).
+constexpr double ct_sin(double x) {
+  double term = x, sum = x;
+  for (int n = 1; n < 40; ++n) {
+    term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double ct_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n < 40; ++n) {
+    term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    sum += term;
+  }
+  return sum;
+}
+
+// W_LEN^K for direction DIR (-1: exp(-2 pi i K / LEN), +1: exp(+2 pi i K / LEN)).
+template <int K, int LEN, int DIR>
+struct Tw {
+  static constexpr double a = DIR * 2.0 * kPi * K / LEN;
+  static constexpr float re = (float)ct_cos(a);
+  static constexpr float im = (float)ct_sin(a);
+};
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// ---------------------------------------------------------------------------
+// R-point DFT in registers: radix-2 decimation in time, bit-reversed input
+// order produced by a compile-time register permutation, natural output.
+// ---------------------------------------------------------------------------
+
+template <int DIR, int LEN, int K>
+__device__ __forceinline__ void bfly(float2& a, float2& b) {
+  float2 t;
+  if constexpr (K == 0) {
+    t = b;
+  } else if constexpr (4 * K == LEN) {
+    t = (DIR < 0) ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);  // b * (-/+ i)
+  } else {
+    constexpr float wr = Tw<K, LEN, DIR>::re;
+    constexpr float wi = Tw<K, LEN, DIR>::im;
+    t = make_float2(fmaf(b.x, wr, -b.y * wi), fmaf(b.x, wi, b.y * wr));
+  }
+  b = make_float2(a.x - t.x, a.y - t.y);
+  a = make_float2(a.x + t.x, a.y + t.y);
+}
+
+template <int R, int DIR, int LEN, int... Ks>
+__device__ __forceinline__ void dit_stage(float2* v, std::integer_sequence<int, Ks...>) {
+#pragma unroll
+  for (int i = 0; i < R; i += LEN) {
+    (bfly<DIR, LEN, Ks>(v[i + Ks], v[i + Ks + LEN / 2]), ...);
+  }
+}
+
+template <int R, int DIR, int LEN>
+__device__ __forceinline__ void dit_stages(float2* v) {
+  if constexpr (LEN <= R) {
+    dit_stage<R, DIR, LEN>(v, std::make_integer_sequence<int, LEN / 2>{});
+    dit_stages<R, DIR, LEN * 2>(v);
+  }
+}
+
+template <int R, int... Is>
+__device__ __forceinline__ void brev_perm(float2* v, std::integer_sequence<int, Is...>) {
+  float2 t[R] = {v[ct_brev(Is, ct_log2(R))]...};
+  ((v[Is] = t[Is]), ...);
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dft_reg(float2* v) {
+  if constexpr (R > 1) {
+    brev_perm<R>(v, std::make_integer_sequence<int, R>{});
+    dit_stages<R, DIR, 2>(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// block FFT
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+
+template <int LOGM>
+struct TwTables {
+  static constexpr int LB = LOGM / 2;            // low bits
+  static constexpr int HB = LOGM - LB;           // high bits
+  static constexpr int NLO = 1 << LB;
+  static constexpr int NHI = 1 << HB;
+  static constexpr int N = NLO + NHI;            // float2 entries (HI first, then LO)
+};
+
+// W_M^t for 0 <= t < M from the shared tables (hi first, lo after), conjugated for DIR = +1.
+template <int LOGM, int DIR>
+__device__ __forceinline__ float2 twiddle(const float2* tw, int t) {
+  using TT = TwTables<LOGM>;
+  float2 w = cmul(tw[t >> TT::LB], tw[TT::NHI + (t & (TT::NLO - 1))]);
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+template <int LOGM, int LOGE, int DIR>
+struct BlockFFT {
+  static constexpr int M = 1 << LOGM;
+  static constexpr int E = 1 << LOGE;
+  static constexpr int T = M / E;
+  static constexpr int SMEM_ELEMS = M + M / 32;  // padded buffer
+
+  // Pass over bits [D, D + RB).  FIRST: inputs from `load(i)`; LAST: outputs to
+  // `emit(i, value)`; otherwise through the shared buffer.
+  template <int D, int RB, bool FIRST, bool LAST, class Load, class Emit>
+  __device__ __forceinline__ static void pass(float2* sm, const float2* tw, Load& load, Emit& emit) {
+    constexpr int R = 1 << RB;
+    constexpr int S = E / R;        // sub-transforms per thread
+    constexpr int STRIDE = M / R;   // input stride
+    const int t = threadIdx.x;
+    float2 v[E];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int j = t + T * s;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = j + r * STRIDE;
+        if constexpr (FIRST) v[s * R + r] = load(i);
+        else v[s * R + r] = sm[spad(i)];
+      }
+    }
+    if constexpr (!FIRST) __syncthreads();  // every value of this pass is in registers
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int j = t + T * s;
+      if constexpr (D > 0) {
+        const int jm = j & ((1 << D) - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const int e = (jm * r) << (LOGM - D - RB);
+          v[s * R + r] = cmul(v[s * R + r], twiddle<LOGM, DIR>(tw, e));
+        }
+      }
+      dft_reg<R, DIR>(v + s * R);
+      const int ob = ((j >> D) << (D + RB)) + (j & ((1 << D) - 1));
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int o = ob + (r << D);
+        if constexpr (LAST) emit(o, v[s * R + r]);
+        else sm[spad(o)] = v[s * R + r];
+      }
+    }
+    if constexpr (!LAST) __syncthreads();
+  }
+
+  template <int D, class Load, class Emit>
+  __device__ __forceinline__ static void passes_from(float2* sm, const float2* tw, Load& load, Emit& emit) {
+    constexpr int RB = (LOGM - D) < LOGE ? (LOGM - D) : LOGE;
+    constexpr bool LAST = (D + RB == LOGM);
+    pass<D, RB, D == 0, LAST>(sm, tw, load, emit);
+    if constexpr (!LAST) passes_from<D + RB>(sm, tw, load, emit);
+  }
+
+  // Full transform: x[i] = load(i) for i < M; emit(k, X[k]) for k < M, unnormalised,
+  // X[k] = sum_i x[i] exp(DIR * 2 pi i * i k / M).
+  template <class Load, class Emit>
+  __device__ __forceinline__ static void run(float2* sm, const float2* tw, Load& load, Emit& emit) {
+    passes_from<0>(sm, tw, load, emit);
+  }
+};
+
+}  // namespace atlas

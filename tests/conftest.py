@@ -11,3 +11,11 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+@pytest.fixture(scope="session")
+def built_lib():
+    """Build the CUDA library in-tree (once) and load it."""
+    from paper_2005_10445_gb300 import binding, build
+    build.build()
+    return binding.load()

@@ -1,0 +1,228 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU only).
+
+Bar: detections (code, window, lag, freq_bin) identical; ToA within 1e-3
+samples; score and peak power within 1e-4 relative (FP32 FFT path against
+FP64).  Per-cell statistics: floor and P* within 1e-4 relative, and the lag
+identical unless the oracle's own top two lags are within the tolerance (then
+the GPU lag must be one of the oracle's near-maximal lags).
+"""
+import numpy as np
+import pytest
+
+from oracle import acq
+from paper_2005_10445_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SCORE_RTOL = 1e-4
+TOA_ATOL = 1e-3
+CELL_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(built_lib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def gpu_search(torch, wl, threshold=25.0, capacity=4096, cells=False, **kw):
+    from paper_2005_10445_gb300.binding import Search
+    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, threshold=threshold, fft_len=wl.fft_len, **kw)
+    x = torch.from_numpy(wl.iq().copy()).cuda()
+    dets, n, cell = s.run(x, capacity=capacity, cells=cells)
+    return s, dets, n, cell
+
+
+def compare_detections(gpu, ora):
+    g_keys = [(int(d["code"]), int(d["window"]), int(d["lag"]), int(d["freq_bin"])) for d in gpu]
+    o_keys = [d.key() for d in ora]
+    assert sorted(g_keys) == sorted(o_keys)
+    by = {d.key(): d for d in ora}
+    for d in gpu:
+        o = by[(int(d["code"]), int(d["window"]), int(d["lag"]), int(d["freq_bin"]))]
+        assert d["score"] == pytest.approx(o.score, rel=SCORE_RTOL)
+        assert d["peak_power"] == pytest.approx(o.peak_power, rel=SCORE_RTOL)
+        assert abs(d["toa"] - o.toa) <= TOA_ATOL
+
+
+def compare_cells(torch, wl, gpu_cells, pairs):
+    x = wl.x.astype(np.complex128)
+    for (w, c) in pairs:
+        L = len(wl.chips[c]) * wl.sps
+        N = wl.fft_len or acq.default_fft_len(L)
+        W, hop = acq.window_plan(wl.n_samples, N, L)
+        nv = acq.n_valid_lags(w, W, wl.n_samples, N, L)
+        xw = acq.window_samples(x, w, hop, N)
+        r = acq.replica(wl.chips[c], wl.sps, N)
+        for k, f in enumerate(wl.freqs_hz):
+            corr = acq.corr_fft(acq.mix(xw, float(f), wl.fs_hz), r)
+            P = np.abs(corr) ** 2
+            g = gpu_cells[w, c, k]
+            assert g["valid"] == 1
+            assert g["floor"] == pytest.approx(P.mean(), rel=CELL_RTOL)
+            tau = int(np.argmax(P[:nv]))
+            assert g["p_max"] == pytest.approx(P[tau], rel=CELL_RTOL)
+            if int(g["lag"]) != tau:
+                # only acceptable when the oracle itself cannot separate the two lags
+                assert 0 <= int(g["lag"]) < nv
+                assert P[int(g["lag"])] >= P[tau] * (1 - CELL_RTOL), (w, c, k, int(g["lag"]), tau)
+
+
+def test_tiny_parity(torch_cuda):
+    wl = synth.tiny()
+    s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True)
+    ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len)
+    assert n == len(ora) == 1
+    compare_detections(dets, ora)
+    compare_cells(torch_cuda, wl, cells, [(0, 0)])
+    assert s.device_status() == 0
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_small_parity_all_cells(torch_cuda, seed):
+    """Several windows with a ragged, zero-padded last window, 3 codes,
+    5 bins, sps 4, N = 8192 (M = 2048)."""
+    wl = synth.small(seed=seed)
+    s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True)
+    ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len)
+    assert n == len(ora) >= 3
+    compare_detections(dets, ora)
+    W = cells.shape[0]
+    compare_cells(torch_cuda, wl, cells, [(w, c) for w in range(W) for c in range(len(wl.chips))])
+    # detections come out ordered by (window, code)
+    keys = [(int(d["window"]), int(d["code"])) for d in dets]
+    assert keys == sorted(keys)
+
+
+@pytest.mark.parametrize("n_chips,sps,N", [
+    (400, 1, 1024),      # M = 2^10, no box sum
+    (500, 2, 2048),      # M = 2^10
+    (900, 4, 8192),      # M = 2^11
+    (700, 8, 16384),     # M = 2^11, sps 8
+    (1500, 2, 8192),     # M = 2^12
+    (3000, 4, 32768),    # M = 2^13
+    (5000, 2, 32768),    # M = 2^14
+    (8192, 8, 131072),   # M = 2^14, sps 8 (the realistic code shape)
+])
+def test_sizes_parity(torch_cuda, n_chips, sps, N):
+    L = n_chips * sps
+    S = 2 * N + 3 * (N - L) // 2 + 17   # ragged last window
+    wl = synth.realistic(seed=n_chips + sps, seconds=S / 4e6, n_codes=2, n_chips=n_chips, sps=sps,
+                         fs_hz=4e6, n_tags=2, snr_range=(-8.0, -2.0),
+                         freqs_hz=np.array([-2500.0, 0.0, 2500.0]), min_same_code_gap=2 * N, fft_len=N)
+    s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True)
+    ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len)
+    assert n == len(ora)
+    compare_detections(dets, ora)
+    W = cells.shape[0]
+    pairs = [(w, c) for w in range(W) for c in range(2)]
+    if N >= 65536:
+        pairs = pairs[:2] + pairs[-2:]
+    compare_cells(torch_cuda, wl, cells, pairs)
+
+
+def test_stream_of_exactly_one_code(torch_cuda):
+    """S = L: one window with the single valid lag 0."""
+    chips = synth.random_chips(1000, 5)
+    sps, N, fs = 2, 4096, 2e6
+    x = synth.awgn(2000, 1.0, np.random.default_rng(0))
+    tag = synth.Tag(0, 0.0, 0.0, 0, 10.0, 0.0)
+    synth.inject(x, chips, sps, fs, tag, 1.0)
+    wl = synth.Workload("exact", x, [chips], sps, fs, np.array([0.0, 700.0]), N, [tag], 1.0)
+    s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True)
+    ora, _ = acq.search(wl.x, wl.chips, sps, fs, wl.freqs_hz, N)
+    assert n == len(ora) == 1
+    compare_detections(dets, ora)
+    assert int(dets[0]["lag"]) == 0 and dets[0]["toa"] == 0.0
+    compare_cells(torch_cuda, wl, cells, [(0, 0)])
+
+
+def test_mixed_code_lengths(torch_cuda):
+    """Codes of two lengths form two groups with their own windows."""
+    rng = np.random.default_rng(3)
+    fs, sps = 4e6, 4
+    chips = [synth.random_chips(600, 1), synth.random_chips(1100, 2), synth.random_chips(600, 3)]
+    S = 60000
+    x = synth.awgn(S, 2048.0, rng)
+    tags = [synth.Tag(0, 5000.0, 1500.0, 2, -5.0, 0.1), synth.Tag(1, 21000.0, -1500.0, 0, -6.0, 1.0),
+            synth.Tag(2, 40000.0, 0.0, 1, -4.0, 2.0)]
+    for t in tags:
+        synth.inject(x, chips[t.code], sps, fs, t, 2048.0)
+    wl = synth.Workload("mixed", x, chips, sps, fs, np.array([-1500.0, 0.0, 1500.0]), 0, tags, 2048.0)
+    s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True)
+    ora, _ = acq.search(wl.x, wl.chips, sps, fs, wl.freqs_hz, 0)
+    assert n == len(ora) == 3
+    compare_detections(dets, ora)
+
+
+def test_capacity_overflow_reports_full_count(torch_cuda):
+    wl = synth.small(seed=12)
+    s, full, n_full, _ = gpu_search(torch_cuda, wl)
+    assert n_full >= 3
+    s2, part, n_part, _ = gpu_search(torch_cuda, wl, capacity=2)
+    assert n_part == n_full and len(part) == 2
+    assert part.tobytes() == full[:2].tobytes()
+
+
+def test_repeat_runs_bit_identical(torch_cuda):
+    wl = synth.small(seed=13)
+    from paper_2005_10445_gb300.binding import Search
+    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len)
+    x = torch_cuda.from_numpy(wl.iq().copy()).cuda()
+    a = s.run(x, cells=True)
+    b = s.run(x, cells=True)
+    assert a[0].tobytes() == b[0].tobytes() and a[2].tobytes() == b[2].tobytes()
+
+
+def test_host_buffer_entry_matches_device(torch_cuda):
+    wl = synth.small(seed=11)
+    from paper_2005_10445_gb300.binding import Search
+    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len)
+    x = torch_cuda.from_numpy(wl.iq().copy()).cuda()
+    d_dev, n_dev, _ = s.run(x)
+    d_host, n_host = s.run_host(wl.iq())
+    assert n_dev == n_host and d_dev.tobytes() == d_host.tobytes()
+
+
+def test_windows_per_launch_does_not_change_results(torch_cuda):
+    wl = synth.small(seed=12)
+    _, a, na, ca = gpu_search(torch_cuda, wl, cells=True, windows_per_launch=1)
+    _, b, nb, cb = gpu_search(torch_cuda, wl, cells=True, windows_per_launch=3)
+    assert na == nb and a.tobytes() == b.tobytes() and ca.tobytes() == cb.tobytes()
+
+
+def test_short_stream_rejected(torch_cuda):
+    from paper_2005_10445_gb300.binding import AtlasError, Search
+    wl = synth.small()
+    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len)
+    x = torch_cuda.zeros((100, 2), dtype=torch_cuda.float32, device="cuda")
+    with pytest.raises(AtlasError):
+        s.run(x)
+
+
+def test_realistic_full_size_sampled(torch_cuda):
+    """1 s at 8 MS/s, 16 codes x 8192 chips at sps 8, 31 bins, 40 tags -- the
+    benchmark's launch configuration.  The oracle recomputes every (window,
+    code) pair the GPU reports plus the pair of every injected tag and a few
+    random pairs, bin by bin."""
+    wl = synth.realistic()
+    s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True)
+    assert n == len(dets)
+    W, hop, N = s.windows(0, wl.n_samples)
+    rng = np.random.default_rng(99)
+    pairs = {(int(d["window"]), int(d["code"])) for d in dets}
+    for t in wl.tags:
+        w = min(int(t.delay) // hop, W - 1)
+        pairs.add((w, t.code))
+    pairs |= {(int(rng.integers(0, W)), int(rng.integers(0, 16))) for _ in range(4)}
+    pairs.add((W - 1, 0))
+    ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len, pairs=sorted(pairs))
+    gsel = np.array([d for d in dets if (int(d["window"]), int(d["code"])) in pairs], dtype=dets.dtype)
+    compare_detections(gsel, ora)
+    # every injected tag is found
+    found = {(int(d["code"]), int(d["window"]) * hop + int(d["lag"])) for d in dets}
+    for t in wl.tags:
+        assert (t.code, int(t.delay)) in found
+    compare_cells(torch_cuda, wl, cells, sorted(pairs)[:6] + [(W - 1, 0)])
