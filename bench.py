@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark of the acquisition search on the realistic workload.
+
+Workload (one step = one full search of one stream, every code x every bin):
+1 s of complex64 baseband at 8 MS/s (int16-range Gaussian noise, sigma 2048)
+with 40 injected tags at SNR U[-20, 0] dB, 16 codes of 8192 +/-1 chips at 8
+samples/chip (L = 65536), windows of N = 131072 overlapping by one code
+length (122 windows), 31 carrier-offset bins over +/-15 kHz.  Synthetic,
+seeded; it stands in for the paper's recorded 8 MS/s receiver data.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (bounded sample per step).
+Multi-GPU (torchrun): every rank searches its own stream (weak scaling,
+replicas; no collective on the data path, only a barrier and a max-reduce of
+the timings).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "acquisition Msamples/s (full code x freq-bin search); % HBM roofline"
+UNIT = "Msamples/s"
+WORKLOAD = ("realistic: 1 s complex64 IQ at 8 MS/s, 16 codes x 8192 chips, 8 samples/chip, "
+            "N = 131072 (hop 65536, 122 windows), 31 bins over +/-15 kHz, 40 tags at U[-20, 0] dB")
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+# FP32 FMA peak at the maximum SM clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def flops_per_cell(N: int) -> float:
+    """Algorithmic FP32 flops of one (window, code, bin) cell of the correlation
+    kernel, in the plain method's terms: inverse FFT of N points (5 N log2 N),
+    complex multiply by the code spectrum (6 N), |.|^2 and the floor/argmax
+    reduction (4 N)."""
+    import math
+    return 5.0 * N * math.log2(N) + 6.0 * N + 4.0 * N
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("acq_kernels.cu", "fft_block.cuh"):
+        with open(os.path.join(ROOT, "paper_2005_10445_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the correlation kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_corr_realistic_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"atlas_clocks_{os.getpid()}.csv")
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id is not None:
+            cmd += ["-i", str(gpu_id)]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "power_w_max": max(pw),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_workload(seed: int):
+    from paper_2005_10445_gb300 import synth
+    return synth.realistic(seed=seed)
+
+
+def oracle_sample(wl, n_codes: int, window: int = 1):
+    """Time the FP64 oracle on one window x n_codes (all bins): returns
+    (seconds, equivalent samples).  One window contributes hop new samples for
+    all codes; n_codes of C codes is that fraction of the window's work."""
+    from oracle import acq
+    L = len(wl.chips[0]) * wl.sps
+    W, hop = acq.window_plan(wl.n_samples, wl.fft_len, L)
+    pairs = [(window, c) for c in range(n_codes)]
+    t0 = time.perf_counter()
+    acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len, pairs=pairs)
+    dt = time.perf_counter() - t0
+    return dt, hop * n_codes / len(wl.chips)
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    wl = make_workload(2)
+    n_codes = 2
+    for _ in range(args.warmup):
+        oracle_sample(wl, n_codes)
+    times, samples = [], 0.0
+    for _ in range(args.steps):
+        dt, s = oracle_sample(wl, n_codes)
+        times.append(dt)
+        samples += s
+    total = sum(times)
+    value = samples / total / 1e6
+    sample = f"per step: window 1 x {n_codes} of 16 codes x 31 bins (numpy FP64, single process)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "single host process"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--capacity", type=int, default=4096)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_10445_gb300 import binding
+    from paper_2005_10445_gb300.build import build
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if not os.path.exists(binding.LIB_PATH):
+        build()
+    wl = make_workload(2 + rank)
+    S = wl.n_samples
+    s = binding.Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len)
+    x = torch.from_numpy(wl.iq().copy()).to(dev)
+    cap = args.capacity
+    out = torch.empty(cap * 32, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def step():
+        s.run_ptr(st.cuda_stream, x.data_ptr(), S, out.data_ptr(), cap, cnt.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # timed region: K steps, L2 flushed before each (outside the events)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    s.profile_begin(max_timed=65536)
+    sampler = ClockSampler(gpu_id=None) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(st)
+        step()
+        evs[i][1].record(st)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    prof = s.profile_end()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    count = int(cnt.item())
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = S * world * args.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    h_x = torch.from_numpy(wl.iq().copy()).pin_memory()
+    h_out = torch.empty(cap * 32, dtype=torch.uint8).pin_memory()
+    h_cnt = torch.zeros(1, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        s.run_host_ptr(st.cuda_stream, h_x.data_ptr(), S, h_out.data_ptr(), cap, h_cnt.data_ptr())
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    e2e_t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        s.run_host_ptr(st.cuda_stream, h_x.data_ptr(), S, h_out.data_ptr(), cap, h_cnt.data_ptr())
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = S * world * args.steps / float(e2e_s.item()) / 1e6
+    n_host = int(h_cnt[0])
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    N = wl.fft_len
+    units_per_launch = prof["corr_units"] / max(prof["corr_launches"], 1)
+    corr_avg_ms = prof["corr_ms"] / max(prof["timed_launches"], 1)
+    achieved = units_per_launch * flops_per_cell(N) / (corr_avg_ms / 1e3) / 1e12
+    traffic = ncu_traffic()
+    hbm_bytes_step = S * 8 * (N / (N - len(wl.chips[0]) * wl.sps)) + len(wl.chips) * N * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "samples_per_step_per_gpu": S,
+                   "l2": "flushed before each step (256 MiB write), outside the timed events",
+                   "parallelism": "replicas: one independent stream per GPU",
+                   "detections_per_step": count},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "k_corr (inverse FFT + |.|^2 + floor/argmax per (window, code, bin))",
+                     "units_per_launch": units_per_launch, "avg_launch_ms": corr_avg_ms,
+                     "flops_per_unit": flops_per_cell(N),
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, max clock)",
+                     "kernel_share_of_step": prof["corr_ms"] / total_ms},
+        "hbm": {"algorithmic_bytes_per_step": hbm_bytes_step,
+                "achieved_gbs": hbm_bytes_step / (total_ms / args.steps / 1e3) / 1e9,
+                "frac_of_measured": hbm_bytes_step / (total_ms / args.steps / 1e3) / 1e9 / 6699.8},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": S * 8,
+                "d2h_bytes_per_step": 4 + 32 * min(n_host, cap)},
+        "gpu_launches": prof["launches"],
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        dt, samples = oracle_sample(wl, len(wl.chips))
+        line["cpu_baseline"] = {"value": samples / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "window 1 x 16 codes x 31 bins of the same stream (numpy FP64, "
+                                          f"single process, {dt:.1f} s); Msamples/s = hop / time"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

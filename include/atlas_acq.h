@@ -145,6 +145,29 @@ int atlas_acq_run_cells(atlas_acq_t ctx, void* stream, const float* d_iq, int64_
 int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t n_samples,
                        atlas_detection* h_out, int32_t capacity, int32_t* h_count);
 
+/* Kernel timing collected by the library between atlas_acq_profile_begin and
+ * atlas_acq_profile_end. */
+typedef struct {
+  int64_t launches;       /* kernels of this library launched while profiling */
+  int64_t corr_launches;  /* launches of the per-code correlation kernel (the dominant one) */
+  double  corr_ms;        /* summed device time of those launches (CUDA events on the run's stream) */
+  int64_t corr_units;     /* (window, code, bin) cells those launches processed */
+  int64_t timed_launches; /* correlation launches that had an event pair (<= the pool size) */
+} atlas_acq_profile;
+
+/*
+ * Start collecting kernel timing: allocates a pool of max_timed CUDA event
+ * pairs (so call it outside any timed region) and resets the counters.
+ * While active, every run records an event pair around each launch of the
+ * correlation kernel on the run's stream; launches past the pool size are
+ * counted but not timed.
+ */
+int atlas_acq_profile_begin(atlas_acq_t ctx, int32_t max_timed);
+
+/* Synchronise the device, sum the recorded times into *out, free the events
+ * and stop collecting. */
+int atlas_acq_profile_end(atlas_acq_t ctx, atlas_acq_profile* out);
+
 /* Device status word of the last run (0 = no kernel-side check failed).
  * Synchronises the device. */
 int atlas_acq_last_device_status(atlas_acq_t ctx);

@@ -29,7 +29,8 @@ ATLAS_ERR_DEVICE = -6
 EXPORTED = [
     "atlas_acq_default_opts", "atlas_acq_create", "atlas_acq_windows", "atlas_acq_run",
     "atlas_acq_run_cells", "atlas_acq_run_host", "atlas_acq_last_device_status",
-    "atlas_acq_last_error", "atlas_acq_destroy", "atlas_acq_strerror",
+    "atlas_acq_last_error", "atlas_acq_destroy", "atlas_acq_strerror", "atlas_acq_profile_begin",
+    "atlas_acq_profile_end",
 ]
 
 
@@ -47,6 +48,11 @@ class Cell(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_float), ("fft_len", ctypes.c_int32),
                 ("windows_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("corr_launches", ctypes.c_int64), ("corr_ms", ctypes.c_double),
+                ("corr_units", ctypes.c_int64), ("timed_launches", ctypes.c_int64)]
 
 
 DETECTION_DTYPE = np.dtype([("code", "<i4"), ("window", "<i4"), ("lag", "<i4"), ("freq_bin", "<i4"),
@@ -92,6 +98,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_acq_last_error.restype = ctypes.c_char_p
     lib.atlas_acq_destroy.argtypes = [vp]
     lib.atlas_acq_destroy.restype = None
+    lib.atlas_acq_profile_begin.argtypes = [vp, i32]
+    lib.atlas_acq_profile_begin.restype = ctypes.c_int
+    lib.atlas_acq_profile_end.argtypes = [vp, ctypes.POINTER(Profile)]
+    lib.atlas_acq_profile_end.restype = ctypes.c_int
     lib.atlas_acq_strerror.argtypes = [ctypes.c_int]
     lib.atlas_acq_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -173,6 +183,14 @@ class Search:
                      h_count: int) -> None:
         _check(self._lib.atlas_acq_run_host(self.ctx, stream, h_iq, n_samples, h_out, capacity, h_count),
                self.ctx)
+
+    def profile_begin(self, max_timed: int = 65536) -> None:
+        _check(self._lib.atlas_acq_profile_begin(self.ctx, max_timed), self.ctx)
+
+    def profile_end(self) -> dict:
+        p = Profile()
+        _check(self._lib.atlas_acq_profile_end(self.ctx, ctypes.byref(p)), self.ctx)
+        return {f: getattr(p, f) for f, _ in Profile._fields_}
 
     def device_status(self) -> int:
         return int(self._lib.atlas_acq_last_device_status(self.ctx))

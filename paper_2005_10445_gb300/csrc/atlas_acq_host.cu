@@ -71,6 +71,11 @@ struct atlas_acq_ctx {
   int stage_cap = 0;
   int* d_stage_count = nullptr;
   std::string last_error;
+  // profiling (atlas_acq_profile_begin / _end)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  int ev_used = 0;
+  int64_t prof_launches = 0, prof_corr_launches = 0, prof_corr_units = 0;
 };
 
 namespace {
@@ -141,6 +146,7 @@ void free_ctx(atlas_acq_ctx* ctx) {
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_stage_out);
   cudaFree(ctx->d_stage_count);
+  for (auto e : ctx->ev) cudaEventDestroy(e);
   cudaSetDevice(prev);
   delete ctx;
 }
@@ -294,6 +300,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       a.G = ctx->d_G;
       a.status = ctx->d_status;
       CK(atlas::launch_window_fft(g.logM, a, st));
+      if (ctx->profiling) ctx->prof_launches += 1;
       CorrParams b;
       b.G = ctx->d_G;
       b.D = g.d_spec;
@@ -311,7 +318,18 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       b.K = ctx->K;
       b.Cg = Cg;
       b.status = ctx->d_status;
+      const bool timed = ctx->profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
+      if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
       CK(atlas::launch_corr(g.logM, b, st));
+      if (timed) {
+        CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st));
+        ctx->ev_used += 1;
+      }
+      if (ctx->profiling) {
+        ctx->prof_launches += 1;
+        ctx->prof_corr_launches += 1;
+        ctx->prof_corr_units += (int64_t)nw * Cg * ctx->K;
+      }
       SelectParams c;
       c.part = ctx->d_part;
       c.codes = g.d_codes;
@@ -329,6 +347,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       c.count = d_count;
       c.cells = cells;
       CK(atlas::launch_select(c, st));
+      if (ctx->profiling) ctx->prof_launches += 1;
     }
   }
   if (capacity > 0) {
@@ -345,6 +364,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
     r.capacity = capacity;
     r.count = d_count;
     CK(atlas::launch_refine(r, std::min(capacity, 1024), st));
+    if (ctx->profiling) ctx->prof_launches += 1;
   }
   return ATLAS_OK;
 }
@@ -459,6 +479,38 @@ int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t
     CK(cudaMemcpyAsync(h_out, ctx->d_stage_out, sizeof(atlas_detection) * (size_t)n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
+  return ATLAS_OK;
+}
+
+int atlas_acq_profile_begin(atlas_acq_t ctx, int32_t max_timed) {
+  if (!ctx || max_timed < 0) return ATLAS_ERR_INVALID_ARG;
+  for (auto e : ctx->ev) cudaEventDestroy(e);
+  ctx->ev.assign(2 * (size_t)max_timed, nullptr);
+  for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
+  ctx->ev_used = 0;
+  ctx->prof_launches = ctx->prof_corr_launches = ctx->prof_corr_units = 0;
+  ctx->profiling = true;
+  return ATLAS_OK;
+}
+
+int atlas_acq_profile_end(atlas_acq_t ctx, atlas_acq_profile* out) {
+  if (!ctx || !out) return ATLAS_ERR_INVALID_ARG;
+  CK(cudaDeviceSynchronize());
+  double ms = 0.0;
+  for (int i = 0; i < ctx->ev_used; ++i) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+    ms += t;
+  }
+  out->launches = ctx->prof_launches;
+  out->corr_launches = ctx->prof_corr_launches;
+  out->corr_ms = ms;
+  out->corr_units = ctx->prof_corr_units;
+  out->timed_launches = ctx->ev_used;
+  for (auto e : ctx->ev) cudaEventDestroy(e);
+  ctx->ev.clear();
+  ctx->ev_used = 0;
+  ctx->profiling = false;
   return ATLAS_OK;
 }
 
