@@ -85,7 +85,7 @@ void atlas_acq_default_opts(atlas_acq_opts* opts);
  * Create a search context on the current CUDA device.
  *   chips           host, n_codes concatenated +/-1 int8 chip sequences (copied)
  *   chips_per_code  host, [n_codes] chip counts (each >= 1)
- *   samples_per_chip  sps >= 1; a power of two
+ *   samples_per_chip  sps: a power of two, 1 .. 16
  *   fs_hz           sample rate (> 0)
  *   freq_offsets_hz host, [n_freq] carrier offsets f_k in Hz (copied)
  *   opts            NULL for defaults

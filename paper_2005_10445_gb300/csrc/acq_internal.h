@@ -11,24 +11,29 @@ namespace atlas {
 
 constexpr int kMinLogM = 10;
 constexpr int kMaxLogM = 14;
-constexpr int kMaxSps = 64;
+constexpr int kMaxSps = 16;
 
 // Device status word bits (the kernels OR these in; 0 = all checks passed).
 enum : int {
   kStatusBadIndex = 1,
 };
 
-// Window FFT: one block per (rho, k, window in the launch group).
-struct WindowFftParams {
+// Mix + box sum + decimation: one block per (tile of q, group of bins, window).
+struct MixParams {
   const float2* x;          // stream [S]
   int64_t S;
-  int N, M, sps, hop, W;    // window length, M = N / sps, samples/chip, hop, windows of the code group
+  int N, M, sps, hop;       // window length, M = N / sps, samples/chip, hop
   int w0, nw;               // first window of the launch group, windows in it
   int K;
   const uint64_t* inc;      // [K] phase increment per sample, turns * 2^64 (two's complement)
+  float2* B;                // out [nw][K][sps][M]: B_rho[q] = sum_s y[(sps q + rho + s) mod N]
+};
+
+// Window FFT: one block per (rho, k, window in the launch group), in place.
+struct WindowFftParams {
+  int M, sps, K, nw;
   const float2* tw;         // twiddle tables for log2(M)
-  float2* G;                // out [nw][K][sps][M]
-  int* status;
+  float2* G;                // in: B, out: FFT_M(B) [nw][K][sps][M]
 };
 
 // Per-code inverse FFT and epilogue: one block per (rho, k, window, code).
@@ -82,6 +87,7 @@ struct CodeBankParams {
 };
 
 cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cudaStream_t s);
+cudaError_t launch_mix(const MixParams& p, cudaStream_t s);
 cudaError_t launch_window_fft(int logM, const WindowFftParams& p, cudaStream_t s);
 cudaError_t launch_corr(int logM, const CorrParams& p, cudaStream_t s);
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s);

@@ -18,8 +18,10 @@
 //
 // Kernels, in launch order per group of windows:
 //   k_code_bank   (create time) D_c = conj(FFT_M(chip_c)) / M
-//   k_window_fft  per (rho, k, w): mix (one LO mix per bin, Section 3 step 2),
-//                 box sum, decimate by sps, FFT_M -> G[w][k][rho]
+//   k_mix         per (tile, bins, w): read the window once, mix it for each bin
+//                 (one LO mix per bin, Section 3 step 2), box sum and decimate
+//                 by sps -> B[w][k][rho]
+//   k_window_fft  per (rho, k, w): G = FFT_M(B), in place
 //   k_corr        per (rho, k, w, c): G * D_c -> IFFT_M -> |.|^2 -> sum and
 //                 argmax over the window's valid lags (Section 3 steps 7-8);
 //                 the correlation never leaves the chip
@@ -113,7 +115,76 @@ __global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_code_bank(CodeBankPara
 }
 
 // ---------------------------------------------------------------------------
-// window FFT: mix + box sum + decimate + FFT_M
+// mix + box sum + decimation (one read of each window for all bins)
+// ---------------------------------------------------------------------------
+
+constexpr int kMixQ = 256;   // q values per block (one per thread)
+constexpr int kMixKG = 8;    // bins per block
+constexpr int kMixRow = kMixQ + 2;  // row pitch of the de-interleaved tile (== 2 mod 16: no bank conflicts)
+
+// B_rho[q] = sum_{s<sps} y[(sps q + rho + s) mod N] with y[m] = x_w[m] exp(-2 pi i f m / fs)
+//          = exp(-2 pi i f sps q / fs) * sum_s x_w[sps q + rho + s] exp(-2 pi i f (rho + s) / fs),
+// the index rho + s >= sps reaching into column q + 1; column M (past the window end)
+// wraps to the window start, whose phase is that of m - N: one extra factor exp(+2 pi i f N / fs).
+template <int SPS>
+__global__ void __launch_bounds__(kMixQ) k_mix(MixParams p) {
+  __shared__ float2 X[SPS * kMixRow];
+  __shared__ float2 inner[kMixKG][2 * SPS];
+  const int q0 = blockIdx.x * kMixQ;
+  const int k0 = blockIdx.y * kMixKG;
+  const int nk = min(kMixKG, p.K - k0);
+  const int wl = blockIdx.z;
+  const int64_t base = (int64_t)(p.w0 + wl) * p.hop;
+  const int N = p.N;
+  for (int i = threadIdx.x; i < SPS * (kMixQ + 1); i += kMixQ) {
+    int t = SPS * q0 + i;
+    if (t >= N) t -= N;
+    const int64_t idx = base + t;
+    X[(i % SPS) * kMixRow + i / SPS] = idx < p.S ? p.x[idx] : make_float2(0.f, 0.f);
+  }
+  for (int i = threadIdx.x; i < nk * 2 * SPS; i += kMixQ) {
+    const int kk = i / (2 * SPS), j = i % (2 * SPS);
+    const uint64_t inc = p.inc[k0 + kk];
+    inner[kk][j] = j < 2 * SPS - 1 ? expi_neg(inc * (uint64_t)j) : expi_neg((uint64_t)0 - inc * (uint64_t)N);
+  }
+  __syncthreads();
+  const int ql = threadIdx.x;
+  const int q = q0 + ql;
+  float2 xa[SPS], xb[SPS];
+#pragma unroll
+  for (int r = 0; r < SPS; ++r) {
+    xa[r] = X[r * kMixRow + ql];
+    xb[r] = X[r * kMixRow + ql + 1];
+  }
+  const bool last = (q == p.M - 1);
+  for (int kk = 0; kk < nk; ++kk) {
+    const int k = k0 + kk;
+    const float2 outer = expi_neg(p.inc[k] * (uint64_t)SPS * (uint64_t)q);
+    const float2 wrap = last ? inner[kk][2 * SPS - 1] : make_float2(1.f, 0.f);
+    float2* Bk = p.B + (((int64_t)wl * p.K + k) * SPS) * p.M + q;
+#pragma unroll
+    for (int rho = 0; rho < SPS; ++rho) {
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int s = 0; s < SPS; ++s) {
+        const int j = rho + s;
+        const float2 w = inner[kk][j];
+        if (j < SPS) {
+          a0.x = fmaf(xa[j].x, w.x, fmaf(-xa[j].y, w.y, a0.x));
+          a0.y = fmaf(xa[j].x, w.y, fmaf(xa[j].y, w.x, a0.y));
+        } else {
+          a1.x = fmaf(xb[j - SPS].x, w.x, fmaf(-xb[j - SPS].y, w.y, a1.x));
+          a1.y = fmaf(xb[j - SPS].x, w.y, fmaf(xb[j - SPS].y, w.x, a1.y));
+        }
+      }
+      const float2 acc = cadd(a0, cmul(a1, wrap));
+      Bk[(int64_t)rho * p.M] = cmul(acc, outer);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// window FFT: G = FFT_M(B), in place
 // ---------------------------------------------------------------------------
 
 template <int LOGM>
@@ -122,40 +193,13 @@ __global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_window_fft(WindowFftPa
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   float2* sm_tw = sm + FFT::SMEM_ELEMS;
-  float2* sm_in = sm_tw + TwTables<LOGM>::N;  // [sps] inner phases, then the wrap factor
-
-  const int rho = blockIdx.x, k = blockIdx.y, wl = blockIdx.z;
-  const int w = p.w0 + wl;
-  const int sps = p.sps;
-  const uint64_t inc = p.inc[k];
   load_tables<LOGM>(sm_tw, p.tw);
-  for (int s = threadIdx.x; s < sps; s += blockDim.x) sm_in[s] = expi_neg(inc * (uint64_t)(rho + s));
-  if (threadIdx.x == 0) sm_in[sps] = expi_neg((uint64_t)0 - inc * (uint64_t)p.N);  // exp(+2 pi i f N / fs)
   __syncthreads();
-
-  const float2* x = p.x;
-  const int64_t base = (int64_t)w * p.hop;
-  const int64_t S = p.S;
-  const int N = p.N;
-  const uint64_t inc_q = inc * (uint64_t)sps;
-  // B_rho[q] = exp(-2 pi i f sps q / fs) * sum_s x_w[sps q + rho + s] exp(-2 pi i f (rho + s) / fs),
-  // with window-relative indices taken mod N (the last q wraps to the window start).
-  auto load = [&](int q) {
-    float2 acc = make_float2(0.f, 0.f);
-    const int m0 = q * sps + rho;
-    for (int s = 0; s < sps; ++s) {
-      int m = m0 + s;
-      float2 wv = sm_in[s];
-      if (m >= N) {
-        m -= N;
-        wv = cmul(wv, sm_in[sps]);
-      }
-      const int64_t idx = base + m;
-      if (idx < S) acc = cadd(acc, cmul(x[idx], wv));
-    }
-    return cmul(acc, expi_neg(inc_q * (uint64_t)q));
-  };
-  float2* G = p.G + (((int64_t)wl * p.K + k) * sps + rho) * FFT::M;
+  // every input value is read into registers/shared memory before the first
+  // output is written (the passes are separated by block barriers), so the
+  // transform can overwrite its own input row
+  float2* G = p.G + (((int64_t)blockIdx.z * p.K + blockIdx.y) * p.sps + blockIdx.x) * FFT::M;
+  auto load = [&](int i) { return G[i]; };
   auto emit = [&](int i, float2 v) { G[i] = v; };
   FFT::run(sm, sm_tw, load, emit);
 }
@@ -209,23 +253,24 @@ __global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_corr(CorrParams p) {
 // selection and ordered compaction (one block per launch group)
 // ---------------------------------------------------------------------------
 
-constexpr int kSelectThreads = 256;
+constexpr int kSelectThreads = 512;  // one warp per (window, code) pair
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(SelectParams p) {
-  __shared__ int scan[kSelectThreads];
+  __shared__ int flags[kSelectThreads / 32];
+  __shared__ atlas_detection recs[kSelectThreads / 32];
   __shared__ int base_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) base_sh = *p.count;
-  __syncthreads();
   const int n_pairs = p.nw * p.Cg;
-  for (int p0 = 0; p0 < n_pairs; p0 += kSelectThreads) {
-    const int pi = p0 + threadIdx.x;
-    int flag = 0, wl = 0, c = 0, bk = 0, btau = 0;
-    float bscore = -1.f, bpmax = 0.f;
+  for (int p0 = 0; p0 < n_pairs; p0 += kSelectThreads / 32) {
+    const int pi = p0 + warp;
+    int flag = 0;
     if (pi < n_pairs) {
-      wl = pi / p.Cg;
-      c = pi % p.Cg;
+      const int wl = pi / p.Cg, c = pi % p.Cg;
       const int w = p.w0 + wl;
-      for (int k = 0; k < p.K; ++k) {
+      float bscore = -1.f, bpmax = 0.f;
+      int bk = 0x7fffffff, btau = 0;
+      for (int k = lane; k < p.K; k += 32) {
         const float4* pr = p.part + (((int64_t)wl * p.Cg + c) * p.K + k) * p.sps;
         float sum = 0.f, best = -1.f;
         int bt = 0x7fffffff;
@@ -244,40 +289,51 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(SelectParams p) {
           cell.valid = 1;
           p.cells[((int64_t)w * p.C + p.codes[c]) * p.K + k] = cell;
         }
-        if (score > bscore) {
+        if (score > bscore) {  // k increases along the loop: ties keep the smaller bin
           bscore = score;
           bk = k;
           btau = bt;
           bpmax = best;
         }
       }
-      flag = bscore >= p.threshold ? 1 : 0;
-    }
-    // inclusive scan of the flags (Hillis-Steele in shared memory)
-    scan[threadIdx.x] = flag;
-    __syncthreads();
-    for (int o = 1; o < kSelectThreads; o <<= 1) {
-      const int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
-      __syncthreads();
-      scan[threadIdx.x] += v;
-      __syncthreads();
-    }
-    if (flag) {
-      const int pos = base_sh + scan[threadIdx.x] - 1;
-      if (pos < p.capacity) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, bscore, o);
+        const int k2 = __shfl_down_sync(0xffffffffu, bk, o);
+        const int t2 = __shfl_down_sync(0xffffffffu, btau, o);
+        const float p2 = __shfl_down_sync(0xffffffffu, bpmax, o);
+        if (s2 > bscore || (s2 == bscore && k2 < bk)) {
+          bscore = s2;
+          bk = k2;
+          btau = t2;
+          bpmax = p2;
+        }
+      }
+      if (lane == 0) {
+        flag = bscore >= p.threshold ? 1 : 0;
         atlas_detection d;
         d.code = p.codes[c];
-        d.window = p.w0 + wl;
+        d.window = w;
         d.lag = btau;
         d.freq_bin = bk;
         d.score = bscore;
         d.peak_power = bpmax;
         d.toa = 0.0;
-        p.out[pos] = d;
+        recs[warp] = d;
       }
     }
+    if (lane == 0) flags[warp] = flag;
     __syncthreads();
-    if (threadIdx.x == 0) base_sh += scan[kSelectThreads - 1];
+    if (threadIdx.x == 0) {  // ordered compaction of this round's pairs
+      int n = base_sh;
+      for (int i = 0; i < kSelectThreads / 32; ++i) {
+        if (flags[i]) {
+          if (n < p.capacity) p.out[n] = recs[i];
+          ++n;
+        }
+      }
+      base_sh = n;
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) *p.count = base_sh;
@@ -422,6 +478,19 @@ cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cud
 #define CALL(LM) k_code_bank<LM><<<n_codes, fft_threads<LM>(), fft_smem<LM>(), s>>>(p)
   ATLAS_DISPATCH_LOGM(logM, CALL)
 #undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mix(const MixParams& p, cudaStream_t s) {
+  dim3 grid(p.M / kMixQ, (p.K + kMixKG - 1) / kMixKG, p.nw);
+  switch (p.sps) {
+    case 1: k_mix<1><<<grid, kMixQ, 0, s>>>(p); break;
+    case 2: k_mix<2><<<grid, kMixQ, 0, s>>>(p); break;
+    case 4: k_mix<4><<<grid, kMixQ, 0, s>>>(p); break;
+    case 8: k_mix<8><<<grid, kMixQ, 0, s>>>(p); break;
+    case 16: k_mix<16><<<grid, kMixQ, 0, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -284,23 +284,28 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
     const int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
     for (int w0 = 0; w0 < W; w0 += wc) {
       const int nw = std::min(wc, W - w0);
+      atlas::MixParams m;
+      m.x = x;
+      m.S = S;
+      m.N = g.N;
+      m.M = g.M;
+      m.sps = ctx->sps;
+      m.hop = g.hop;
+      m.w0 = w0;
+      m.nw = nw;
+      m.K = ctx->K;
+      m.inc = ctx->d_inc;
+      m.B = ctx->d_G;
+      CK(atlas::launch_mix(m, st));
       WindowFftParams a;
-      a.x = x;
-      a.S = S;
-      a.N = g.N;
       a.M = g.M;
       a.sps = ctx->sps;
-      a.hop = g.hop;
-      a.W = W;
-      a.w0 = w0;
-      a.nw = nw;
       a.K = ctx->K;
-      a.inc = ctx->d_inc;
+      a.nw = nw;
       a.tw = g.d_tw;
       a.G = ctx->d_G;
-      a.status = ctx->d_status;
       CK(atlas::launch_window_fft(g.logM, a, st));
-      if (ctx->profiling) ctx->prof_launches += 1;
+      if (ctx->profiling) ctx->prof_launches += 2;
       CorrParams b;
       b.G = ctx->d_G;
       b.D = g.d_spec;

@@ -17,7 +17,9 @@
 // writes of the first pass are free of bank conflicts.
 //
 // Twiddles W_M^t come from two small tables, W_M^t = HI[t >> LB] * LO[t & (2^LB - 1)],
-// each entry the correctly rounded FP32 value of a FP64 evaluation.
+// each entry the correctly rounded FP32 value of a FP64 evaluation; within a
+// pass a thread takes every eighth power of its base twiddle from the tables
+// and the powers in between by repeated multiplication.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -181,11 +183,16 @@ struct BlockFFT {
     for (int s = 0; s < S; ++s) {
       const int j = t + T * s;
       if constexpr (D > 0) {
+        // W^{jm r}: every eighth power from the tables, the others by one to
+        // seven multiplications by W^{jm} (a few ulps at most)
         const int jm = j & ((1 << D) - 1);
+        constexpr int SH = LOGM - D - RB;
+        const float2 w1 = twiddle<LOGM, DIR>(tw, jm << SH);
+        float2 w = w1;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const int e = (jm * r) << (LOGM - D - RB);
-          v[s * R + r] = cmul(v[s * R + r], twiddle<LOGM, DIR>(tw, e));
+          if (r > 1) w = (r & 7) == 0 ? twiddle<LOGM, DIR>(tw, (jm * r) << SH) : cmul(w, w1);
+          v[s * R + r] = cmul(v[s * R + r], w);
         }
       }
       dft_reg<R, DIR>(v + s * R);

@@ -82,6 +82,7 @@ def test_create_rejects_unsupported_sizes(lib):
     ch = np.ones(40000, np.int8)
     assert _create(lib, ch, [40000], 1, 1, 1e6, [0.0], 1) == U        # N/sps = 2^17 > 2^14
     assert _create(lib, ch[:100], [100], 1, 3, 1e6, [0.0], 1) == U    # sps not a power of two
+    assert _create(lib, ch[:100], [100], 1, 32, 1e6, [0.0], 1) == U   # sps above 16
     o = binding.default_opts()
     o.fft_len = 3000                                                  # not a power of two
     assert _create(lib, ch[:100], [100], 1, 2, 1e6, [0.0], 1, o) == U

@@ -105,6 +105,7 @@ def test_small_parity_all_cells(torch_cuda, seed):
     (3000, 4, 32768),    # M = 2^13
     (5000, 2, 32768),    # M = 2^14
     (8192, 8, 131072),   # M = 2^14, sps 8 (the realistic code shape)
+    (600, 16, 16384),    # M = 2^10, sps 16
 ])
 def test_sizes_parity(torch_cuda, n_chips, sps, N):
     L = n_chips * sps
