@@ -168,6 +168,35 @@ int atlas_acq_profile_begin(atlas_acq_t ctx, int32_t max_timed);
  * and stop collecting. */
 int atlas_acq_profile_end(atlas_acq_t ctx, atlas_acq_profile* out);
 
+/*
+ * Search for one code without a context and without allocating device
+ * memory.  The paper has no counterpart: it exists for callers that cannot
+ * call cudaMalloc when they need a search -- code under a framework whose
+ * caching allocator owns device memory and forbids raw allocations, plug-ins
+ * that must not grow the process's footprint, or a real-time loop that cannot
+ * afford an allocation's implicit synchronisation.
+ *   stream, d_iq, n_samples, d_out, capacity, d_count  as in atlas_acq_run
+ *   d_chips        device, [n_chips] +/-1 int8 chips of the one code (caller-owned)
+ *   samples_per_chip, fs_hz  as in atlas_acq_create
+ *   freq_offsets_hz  host, [n_freq] carrier offsets in Hz (read during the call)
+ *   fft_len        N; 0 = 2 * nextpow2(n_chips * samples_per_chip)
+ *   threshold      detection threshold on P_max / floor
+ * All intermediate arrays live in one static device array of about 4.3 MiB
+ * that each GPU loading the library keeps until the process exits.  Limits:
+ * N <= 16384, n_freq <= 32, samples_per_chip a power of two <= 16,
+ * N / samples_per_chip >= 1024; beyond them the call returns
+ * ATLAS_ERR_UNSUPPORTED and does no device work.  The first call on a device
+ * looks up the array's device address (and sets kernel attributes); make that
+ * first call before any stream capture.  Every call reuses the same array and
+ * rewrites what it reads; calls whose device work may overlap (other host
+ * threads, or streams not ordered with this one) race on it.  Results match
+ * atlas_acq_run for the same code; the call is asynchronous on `stream`.
+ */
+int atlas_acq_run_static(void* stream, const float* d_iq, int64_t n_samples, const int8_t* d_chips,
+                         int32_t n_chips, int32_t samples_per_chip, double fs_hz,
+                         const double* freq_offsets_hz, int32_t n_freq, int32_t fft_len, float threshold,
+                         atlas_detection* d_out, int32_t capacity, int32_t* d_count);
+
 /* Device status word of the last run (0 = no kernel-side check failed).
  * Synchronises the device. */
 int atlas_acq_last_device_status(atlas_acq_t ctx);

@@ -30,7 +30,7 @@ EXPORTED = [
     "atlas_acq_default_opts", "atlas_acq_create", "atlas_acq_windows", "atlas_acq_run",
     "atlas_acq_run_cells", "atlas_acq_run_host", "atlas_acq_last_device_status",
     "atlas_acq_last_error", "atlas_acq_destroy", "atlas_acq_strerror", "atlas_acq_profile_begin",
-    "atlas_acq_profile_end",
+    "atlas_acq_profile_end", "atlas_acq_run_static",
 ]
 
 
@@ -102,6 +102,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_acq_profile_begin.restype = ctypes.c_int
     lib.atlas_acq_profile_end.argtypes = [vp, ctypes.POINTER(Profile)]
     lib.atlas_acq_profile_end.restype = ctypes.c_int
+    lib.atlas_acq_run_static.argtypes = [vp, vp, i64, vp, i32, i32, f64, vp, i32, i32, ctypes.c_float, vp, i32, vp]
+    lib.atlas_acq_run_static.restype = ctypes.c_int
     lib.atlas_acq_strerror.argtypes = [ctypes.c_int]
     lib.atlas_acq_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -234,3 +236,13 @@ class Search:
         self.run_host_ptr(stream, x_iq.ctypes.data, x_iq.shape[0], out.ctypes.data, capacity, cnt.ctypes.data)
         n = int(cnt[0])
         return out[: min(n, capacity)].copy(), n
+
+
+def run_static_ptr(stream: int, d_iq: int, n_samples: int, d_chips: int, n_chips: int, samples_per_chip: int,
+                   fs_hz: float, freq_offsets_hz, fft_len: int, threshold: float, d_out: int, capacity: int,
+                   d_count: int) -> None:
+    """atlas_acq_run_static: one code, no context, no device allocation."""
+    fr = np.ascontiguousarray(np.asarray(freq_offsets_hz, np.float64))
+    _check(load().atlas_acq_run_static(stream, d_iq, n_samples, d_chips, n_chips, samples_per_chip, float(fs_hz),
+                                       fr.ctypes.data, len(fr), fft_len, float(threshold), d_out, capacity,
+                                       d_count))
