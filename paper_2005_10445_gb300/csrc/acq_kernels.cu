@@ -234,15 +234,17 @@ __global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_corr(CorrParams p) {
   const float2* G = p.G + (((int64_t)wl * p.K + k) * sps + rho) * FFT::M;
   const float2* D = p.D + (int64_t)c * FFT::M;
   auto load = [&](int i) { return cmul(G[i], D[i]); };
+  // lag tau = sps*q + rho is valid iff q < qlim
+  const int qlim = (nvalid - rho + sps - 1) / sps;
   float sum = 0.f, best = -1.f;
-  int bt = 0x7fffffff;
+  int bq = 0x7fffffff;
   auto emit = [&](int q, float2 v) {
     const float P = fmaf(v.x, v.x, v.y * v.y);
     sum += P;
-    const int tau = q * sps + rho;
-    if (tau < nvalid) better(best, bt, P, tau);
+    if (q < qlim) better(best, bq, P, q);
   };
   FFT::run(sm, sm_tw, load, emit);
+  int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
   block_reduce_stats(sum, best, bt, red);
   if (threadIdx.x == 0) {
     p.part[(((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho] = make_float4(sum, best, __int_as_float(bt), 0.f);

@@ -90,9 +90,14 @@ __device__ __forceinline__ void bfly(float2& a, float2& b) {
   } else if constexpr (4 * K == LEN) {
     t = (DIR < 0) ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);  // b * (-/+ i)
   } else {
+    // a + w b by four fused multiply-adds, then a - w b = 2a - (a + w b) by two more
     constexpr float wr = Tw<K, LEN, DIR>::re;
     constexpr float wi = Tw<K, LEN, DIR>::im;
-    t = make_float2(fmaf(b.x, wr, -b.y * wi), fmaf(b.x, wi, b.y * wr));
+    const float px = fmaf(b.x, wr, fmaf(-b.y, wi, a.x));
+    const float py = fmaf(b.x, wi, fmaf(b.y, wr, a.y));
+    b = make_float2(fmaf(2.f, a.x, -px), fmaf(2.f, a.y, -py));
+    a = make_float2(px, py);
+    return;
   }
   b = make_float2(a.x - t.x, a.y - t.y);
   a = make_float2(a.x + t.x, a.y + t.y);
@@ -165,20 +170,29 @@ struct BlockFFT {
   __device__ __forceinline__ static void pass(float2* sm, const float2* tw, Load& load, Emit& emit) {
     constexpr int R = 1 << RB;
     constexpr int S = E / R;        // sub-transforms per thread
-    constexpr int STRIDE = M / R;   // input stride
+    constexpr int STRIDE = M / R;   // input stride (a multiple of 32)
+    static_assert(STRIDE % 32 == 0 && T % 32 == 0, "padding arithmetic needs 32-multiples");
+    static_assert(D == 0 || D >= 5, "output strides below 32 are not used with 32 values per thread");
+    // padded shared index spad(i) = i + i/32 of every access below is a
+    // per-thread base plus a compile-time offset
+    constexpr int PSTRIDE = STRIDE + STRIDE / 32;
+    constexpr int PT = T + T / 32;
+    constexpr int POUT = D == 0 ? 1 : (1 << D) + (1 << (D - 5));
     const int t = threadIdx.x;
     float2 v[E];
+    if constexpr (FIRST) {
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const int j = t + T * s;
+      for (int s = 0; s < S; ++s)
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = j + r * STRIDE;
-        if constexpr (FIRST) v[s * R + r] = load(i);
-        else v[s * R + r] = sm[spad(i)];
-      }
+        for (int r = 0; r < R; ++r) v[s * R + r] = load(t + T * s + r * STRIDE);
+    } else {
+      const float2* src = sm + spad(t);
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[s * R + r] = src[s * PT + r * PSTRIDE];
+      __syncthreads();  // every value of this pass is in registers
     }
-    if constexpr (!FIRST) __syncthreads();  // every value of this pass is in registers
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const int j = t + T * s;
@@ -197,11 +211,13 @@ struct BlockFFT {
       }
       dft_reg<R, DIR>(v + s * R);
       const int ob = ((j >> D) << (D + RB)) + (j & ((1 << D) - 1));
+      if constexpr (LAST) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int o = ob + (r << D);
-        if constexpr (LAST) emit(o, v[s * R + r]);
-        else sm[spad(o)] = v[s * R + r];
+        for (int r = 0; r < R; ++r) emit(ob + (r << D), v[s * R + r]);
+      } else {
+        float2* dst = sm + spad(ob);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[r * POUT] = v[s * R + r];
       }
     }
     if constexpr (!LAST) __syncthreads();
