@@ -75,7 +75,9 @@ typedef struct {
   float   threshold;       /* detection threshold on P_max / floor; default 25 */
   int32_t fft_len;         /* N for every code; 0 = 2 * nextpow2(L_c) per code */
   int32_t windows_per_launch; /* windows processed per launch group; 0 = automatic */
-  int32_t reserved[5];
+  int32_t tile_log2;       /* complex values per thread of the transform kernels: 4 -> 16, 5 -> 32;
+                              0 = default (32) or the autotuned choice */
+  int32_t reserved[4];
 } atlas_acq_opts;
 
 /* Fill *opts with the defaults. */
@@ -93,8 +95,8 @@ void atlas_acq_default_opts(atlas_acq_opts* opts);
  * transformed replicas are computed once and kept), allocates every
  * workspace the searches need (Section 4.2: preallocated, size-keyed arrays
  * that are reused), and synchronises the device before returning.
- * Supported sizes: N a power of two with N >= L_c, N/sps between 2^10 and
- * 2^14; otherwise ATLAS_ERR_UNSUPPORTED.  Ownership: *out is owned by the
+ * Supported sizes: N a power of two with N > L_c, N/sps between 2^10 and
+ * 2^15; otherwise ATLAS_ERR_UNSUPPORTED.  Ownership: *out is owned by the
  * caller and released with atlas_acq_destroy().
  */
 int atlas_acq_create(atlas_acq_t* out, const int8_t* chips, const int32_t* chips_per_code,

@@ -47,7 +47,8 @@ class Cell(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_float), ("fft_len", ctypes.c_int32),
-                ("windows_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("windows_per_launch", ctypes.c_int32), ("tile_log2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Profile(ctypes.Structure):
@@ -133,7 +134,7 @@ class Search:
 
     def __init__(self, chips: Sequence[np.ndarray], samples_per_chip: int, fs_hz: float,
                  freq_offsets_hz: Sequence[float], threshold: float = 25.0, fft_len: int = 0,
-                 windows_per_launch: int = 0):
+                 windows_per_launch: int = 0, tile_log2: int = 0):
         lib = load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -144,6 +145,7 @@ class Search:
         o.threshold = threshold
         o.fft_len = fft_len
         o.windows_per_launch = windows_per_launch
+        o.tile_log2 = tile_log2
         self.n_codes = len(chips)
         self.n_freq = len(fr)
         st = lib.atlas_acq_create(ctypes.byref(self.ctx), cat.ctypes.data, cpc.ctypes.data, len(chips),

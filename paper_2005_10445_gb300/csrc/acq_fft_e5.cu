@@ -1,0 +1,14 @@
+// acq_fft_e5.cu -- transform kernels with 32 complex values per thread.
+#include "acq_fft_kernels.cuh"
+
+namespace atlas {
+
+cudaError_t prepare_fft_e5() { return FftLaunch<5>::prepare(); }
+
+cudaError_t launch_window_fft_e5(int logM, const WindowFftParams& p, cudaStream_t s) {
+  return FftLaunch<5>::window_fft(logM, p, s);
+}
+
+cudaError_t launch_corr_e5(int logM, const CorrParams& p, cudaStream_t s) { return FftLaunch<5>::corr(logM, p, s); }
+
+}  // namespace atlas

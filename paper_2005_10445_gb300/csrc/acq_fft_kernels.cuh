@@ -1,0 +1,237 @@
+// acq_fft_kernels.cuh -- the transform kernels of the search, templated on the
+// transform size (LOGM) and on the tile shape (LOGE: 2^LOGE complex values per
+// thread, 2^(LOGM-LOGE) threads per block).  Instantiated once per LOGE in
+// acq_fft_e4.cu / acq_fft_e5.cu; the host picks the tile shape per size
+// (autotuned or default).
+//
+//   k_window_fft<LOGM, LOGE>        G = FFT_M(B) in place, one block per (rho, k, window)
+//   k_corr<LOGM, LOGE>              G * conj(C) / M -> IFFT_M -> |.|^2 -> floor sum, argmax
+//   k_window_fft_split<LOGH, LOGE>  M = 2^(LOGH+1): a 2-block cluster, block h transforms the
+//                                   even (h = 0) or odd (h = 1) samples of the row; the row
+//                                   becomes [E | O] (decimation in time)
+//   k_corr_split<LOGH, LOGE>        rebuilds G from E and O on load, multiplies by the code
+//                                   spectrum, takes one radix-2 decimation-in-frequency step
+//                                   and inverse-transforms one half: block h produces the
+//                                   lags q = 2k + h
+// Section 4.1 computes cross-correlations with FFTs; the split forms are the
+// same transforms with one radix-2 stage folded into the global loads, so
+// transforms of 2^15 points need no more shared memory than 2^14.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "acq_common.cuh"
+
+namespace atlas {
+
+template <int LOGM, int LOGE>
+constexpr int fft_threads() { return (1 << LOGM) >> LOGE; }
+
+// dynamic shared memory: padded transform buffer, twiddle tables of the
+// transform (and of the split stage), reduction scratch for up to 32 warps
+template <int LOGM>
+constexpr size_t fft_smem() {
+  return sizeof(float2) * (BlockFFT<LOGM, 5, -1>::SMEM_ELEMS + TwTables<LOGM>::N + TwTables<LOGM + 1>::N) +
+         32 * sizeof(float4) + sizeof(float2) * (kMaxSps + 1);
+}
+
+// valid lags of window w (Section 2.1 overlap rule): [0, hop) before the last
+// window, [0, min(hop, S - L - w*hop)] in the last.
+__device__ __forceinline__ int valid_lags(const CorrParams& p, int w) {
+  int nvalid = p.hop;
+  if (w == p.W - 1) {
+    const int64_t lim = p.S - p.L - (int64_t)w * p.hop;
+    nvalid = (int)(lim < p.hop ? lim : p.hop) + 1;
+  }
+  return nvalid;
+}
+
+template <int LOGM, int LOGE>
+__global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_window_fft(WindowFftParams p) {
+  using FFT = BlockFFT<LOGM, LOGE, -1>;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  load_tables<LOGM>(sm_tw, p.tw);
+  __syncthreads();
+  // every input value is read into registers/shared memory before the first
+  // output is written (the passes are separated by block barriers), so the
+  // transform can overwrite its own input row
+  float2* G = p.G + (((int64_t)blockIdx.z * p.K + blockIdx.y) * p.sps + blockIdx.x) * FFT::M;
+  auto load = [&](int i) { return G[i]; };
+  auto emit = [&](int i, float2 v) { G[i] = v; };
+  FFT::run(sm, sm_tw, load, emit);
+}
+
+template <int LOGM, int LOGE>
+__global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p) {
+  using FFT = BlockFFT<LOGM, LOGE, +1>;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + TwTables<LOGM + 1>::N);
+
+  const int rho = blockIdx.x, k = blockIdx.y;
+  const int wl = blockIdx.z / p.Cg, c = blockIdx.z % p.Cg;
+  const int sps = p.sps;
+  load_tables<LOGM>(sm_tw, p.tw);
+  __syncthreads();
+  const int nvalid = valid_lags(p, p.w0 + wl);
+
+  const float2* G = p.G + (((int64_t)wl * p.K + k) * sps + rho) * FFT::M;
+  const float2* D = p.D + (int64_t)c * FFT::M;
+  auto load = [&](int i) { return cmul(G[i], D[i]); };
+  // lag tau = sps*q + rho is valid iff q < qlim
+  const int qlim = (nvalid - rho + sps - 1) / sps;
+  float sum = 0.f, best = -1.f;
+  int bq = 0x7fffffff;
+  auto emit = [&](int q, float2 v) {
+    const float P = fmaf(v.x, v.x, v.y * v.y);
+    sum += P;
+    if (q < qlim) better(best, bq, P, q);
+  };
+  FFT::run(sm, sm_tw, load, emit);
+  int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
+  block_reduce_stats(sum, best, bt, red);
+  if (threadIdx.x == 0) {
+    p.part[(((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho] = make_float4(sum, best, __int_as_float(bt), 0.f);
+  }
+}
+
+template <int LOGH, int LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(fft_threads<LOGH, LOGE>())
+    k_window_fft_split(WindowFftParams p) {
+  using FFT = BlockFFT<LOGH, LOGE, -1>;
+  constexpr int H = 1 << LOGH;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  load_tables<LOGH>(sm_tw, p.tw);
+  __syncthreads();
+  const int rho = blockIdx.x >> 1, h = blockIdx.x & 1;
+  float2* row = p.G + (((int64_t)blockIdx.z * p.K + blockIdx.y) * p.sps + rho) * (2 * H);
+  auto load = [&](int i) { return row[2 * i + h]; };
+  auto emit = [&](int k, float2 v) { row[h * H + k] = v; };
+  // both blocks of the cluster have read the whole row before either writes
+  auto hook = [] { cooperative_groups::this_cluster().sync(); };
+  FFT::run(sm, sm_tw, load, emit, hook);
+}
+
+template <int LOGH, int LOGE>
+__global__ void __launch_bounds__(fft_threads<LOGH, LOGE>()) k_corr_split(CorrParams p) {
+  using FFT = BlockFFT<LOGH, LOGE, +1>;
+  constexpr int H = 1 << LOGH;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  float2* sm_tw2 = sm_tw + TwTables<LOGH>::N;
+  float4* red = reinterpret_cast<float4*>(sm_tw2 + TwTables<LOGH + 1>::N);
+
+  const int rho = blockIdx.x >> 1, h = blockIdx.x & 1, k = blockIdx.y;
+  const int wl = blockIdx.z / p.Cg, c = blockIdx.z % p.Cg;
+  const int sps = p.sps;
+  load_tables<LOGH>(sm_tw, p.tw);
+  load_tables<LOGH + 1>(sm_tw2, p.tw2);
+  __syncthreads();
+  const int nvalid = valid_lags(p, p.w0 + wl);
+
+  const float2* E = p.G + (((int64_t)wl * p.K + k) * sps + rho) * (2 * H);
+  const float2* O = E + H;
+  const float2* D = p.D + (int64_t)c * (2 * H);
+  // G[i] = E[i] + W^i O[i], G[i + H] = E[i] - W^i O[i]   (W = exp(-2 pi i / 2H));
+  // h = 0: Z[i] + Z[i + H];  h = 1: (Z[i] - Z[i + H]) W^-i   (Z = G * D)
+  auto load = [&](int i) {
+    const float2 w = twiddle<LOGH + 1, -1>(sm_tw2, i);
+    const float2 wo = cmul(w, O[i]);
+    const float2 e = E[i];
+    const float2 z0 = cmul(make_float2(e.x + wo.x, e.y + wo.y), D[i]);
+    const float2 z1 = cmul(make_float2(e.x - wo.x, e.y - wo.y), D[i + H]);
+    if (h == 0) return make_float2(z0.x + z1.x, z0.y + z1.y);
+    return cmul(make_float2(z0.x - z1.x, z0.y - z1.y), make_float2(w.x, -w.y));
+  };
+  const int qlim = (nvalid - rho + sps - 1) / sps;
+  float sum = 0.f, best = -1.f;
+  int bq = 0x7fffffff;
+  auto emit = [&](int kk, float2 v) {
+    const int q = 2 * kk + h;
+    const float P = fmaf(v.x, v.x, v.y * v.y);
+    sum += P;
+    if (q < qlim) better(best, bq, P, q);
+  };
+  FFT::run(sm, sm_tw, load, emit);
+  int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
+  block_reduce_stats(sum, best, bt, red);
+  if (threadIdx.x == 0) {
+    p.part[(((int64_t)wl * p.Cg + c) * p.K + k) * (2 * sps) + 2 * rho + h] =
+        make_float4(sum, best, __int_as_float(bt), 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers for one tile shape
+// ---------------------------------------------------------------------------
+
+template <int LOGE>
+struct FftLaunch {
+  template <int LOGM>
+  static cudaError_t prepare_one() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_window_fft<LOGM, LOGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fft_smem<LOGM>())) != cudaSuccess)
+      return e;
+    return cudaFuncSetAttribute(k_corr<LOGM, LOGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fft_smem<LOGM>());
+  }
+
+  static cudaError_t prepare() {
+    cudaError_t e;
+    if ((e = prepare_one<10>()) != cudaSuccess) return e;
+    if ((e = prepare_one<11>()) != cudaSuccess) return e;
+    if ((e = prepare_one<12>()) != cudaSuccess) return e;
+    if ((e = prepare_one<13>()) != cudaSuccess) return e;
+    if ((e = prepare_one<14>()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_window_fft_split<14, LOGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fft_smem<14>())) != cudaSuccess)
+      return e;
+    return cudaFuncSetAttribute(k_corr_split<14, LOGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fft_smem<14>());
+  }
+
+  static cudaError_t window_fft(int logM, const WindowFftParams& p, cudaStream_t s) {
+    dim3 grid(p.sps, p.K, p.nw);
+    switch (logM) {
+      case 10: k_window_fft<10, LOGE><<<grid, fft_threads<10, LOGE>(), fft_smem<10>(), s>>>(p); break;
+      case 11: k_window_fft<11, LOGE><<<grid, fft_threads<11, LOGE>(), fft_smem<11>(), s>>>(p); break;
+      case 12: k_window_fft<12, LOGE><<<grid, fft_threads<12, LOGE>(), fft_smem<12>(), s>>>(p); break;
+      case 13: k_window_fft<13, LOGE><<<grid, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
+      case 14: k_window_fft<14, LOGE><<<grid, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p); break;
+      case 15: {
+        dim3 g2(2 * p.sps, p.K, p.nw);
+        k_window_fft_split<14, LOGE><<<g2, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p);
+        break;
+      }
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t corr(int logM, const CorrParams& p, cudaStream_t s) {
+    dim3 grid(p.sps, p.K, p.nw * p.Cg);
+    switch (logM) {
+      case 10: k_corr<10, LOGE><<<grid, fft_threads<10, LOGE>(), fft_smem<10>(), s>>>(p); break;
+      case 11: k_corr<11, LOGE><<<grid, fft_threads<11, LOGE>(), fft_smem<11>(), s>>>(p); break;
+      case 12: k_corr<12, LOGE><<<grid, fft_threads<12, LOGE>(), fft_smem<12>(), s>>>(p); break;
+      case 13: k_corr<13, LOGE><<<grid, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
+      case 14: k_corr<14, LOGE><<<grid, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p); break;
+      case 15: {
+        dim3 g2(2 * p.sps, p.K, p.nw * p.Cg);
+        k_corr_split<14, LOGE><<<g2, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p);
+        break;
+      }
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace atlas

@@ -10,7 +10,7 @@
 namespace atlas {
 
 constexpr int kMinLogM = 10;
-constexpr int kMaxLogM = 14;
+constexpr int kMaxLogM = 15;  // 2^15 via the split (two-block) transforms
 constexpr int kMaxSps = 16;
 
 // Device status word bits (the kernels OR these in; 0 = all checks passed).
@@ -40,8 +40,9 @@ struct WindowFftParams {
 struct CorrParams {
   const float2* G;          // [nw][K][sps][M]
   const float2* D;          // [Cg][M] conj(FFT_M(chips)) / M
-  const float2* tw;
-  float4* part;             // out [nw][Cg][K][sps] = {sum P, P*, tau*, 0}
+  const float2* tw;         // twiddle tables of the block transform
+  const float2* tw2;        // tables of the full size M (split transforms only)
+  float4* part;             // out [nw][Cg][K][sps] (x2 for split) = {sum P, P*, tau*, 0}
   int64_t S;
   int N, M, sps, hop, W, L;
   int w0, nw, K, Cg;
@@ -52,7 +53,7 @@ struct CorrParams {
 struct SelectParams {
   const float4* part;       // [nw][Cg][K][sps]
   const int* codes;         // [Cg] global code ids of the group
-  int Cg, C, K, sps, N, W, w0, nw;
+  int Cg, C, K, sps, N, W, w0, nw;  // sps here: partial results per cell
   float threshold;
   atlas_detection* out;
   int capacity;
@@ -88,8 +89,15 @@ struct CodeBankParams {
 
 cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cudaStream_t s);
 cudaError_t launch_mix(const MixParams& p, cudaStream_t s);
-cudaError_t launch_window_fft(int logM, const WindowFftParams& p, cudaStream_t s);
-cudaError_t launch_corr(int logM, const CorrParams& p, cudaStream_t s);
+// loge: log2 of the complex values per thread of the transform kernels (4 or 5)
+cudaError_t launch_window_fft(int logM, int loge, const WindowFftParams& p, cudaStream_t s);
+cudaError_t launch_corr(int logM, int loge, const CorrParams& p, cudaStream_t s);
+cudaError_t prepare_fft_e4();
+cudaError_t prepare_fft_e5();
+cudaError_t launch_window_fft_e4(int logM, const WindowFftParams& p, cudaStream_t s);
+cudaError_t launch_window_fft_e5(int logM, const WindowFftParams& p, cudaStream_t s);
+cudaError_t launch_corr_e4(int logM, const CorrParams& p, cudaStream_t s);
+cudaError_t launch_corr_e5(int logM, const CorrParams& p, cudaStream_t s);
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s);
 cudaError_t launch_refine(const RefineParams& p, int grid, cudaStream_t s);
 cudaError_t prepare_kernels();  // raises the dynamic shared-memory limits once per process

@@ -33,64 +33,12 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "acq_common.cuh"
+#include "acq_fft_kernels.cuh"
 #include "acq_internal.h"
 #include "fft_block.cuh"
 
 namespace atlas {
-
-constexpr int kLogE = 5;  // 32 complex values per thread
-
-// phase (turns * 2^64) -> exp(-2 pi i turns) in FP32.  The top 32 bits give the
-// angle as a fraction of a half turn in [-1, 1).
-__device__ __forceinline__ float2 expi_neg(uint64_t ph) {
-  const float h = (float)(int32_t)(ph >> 32) * 4.656612873077392578125e-10f;  // 2^-31
-  float s, c;
-  sincospif(h, &s, &c);
-  return make_float2(c, -s);
-}
-
-template <int LOGM>
-__device__ __forceinline__ void load_tables(float2* sm_tw, const float2* tw) {
-  for (int i = threadIdx.x; i < TwTables<LOGM>::N; i += blockDim.x) sm_tw[i] = tw[i];
-}
-
-// Block-wide deterministic reduction of (sum, max, argmax) with the smallest
-// lag on ties.  Result valid in thread 0.
-__device__ __forceinline__ void better(float& best, int& bt, float p, int t) {
-  if (p > best || (p == best && t < bt)) {
-    best = p;
-    bt = t;
-  }
-}
-
-__device__ __forceinline__ void block_reduce_stats(float& sum, float& best, int& bt, float4* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float s2 = __shfl_down_sync(0xffffffffu, sum, o);
-    const float b2 = __shfl_down_sync(0xffffffffu, best, o);
-    const int t2 = __shfl_down_sync(0xffffffffu, bt, o);
-    sum += s2;
-    better(best, bt, b2, t2);
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) red[warp] = make_float4(sum, best, __int_as_float(bt), 0.f);
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    float4 r = lane < nw ? red[lane] : make_float4(0.f, -1.f, __int_as_float(0x7fffffff), 0.f);
-    sum = r.x;
-    best = r.y;
-    bt = __float_as_int(r.z);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float s2 = __shfl_down_sync(0xffffffffu, sum, o);
-      const float b2 = __shfl_down_sync(0xffffffffu, best, o);
-      const int t2 = __shfl_down_sync(0xffffffffu, bt, o);
-      sum += s2;
-      better(best, bt, b2, t2);
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // code bank (create time)
@@ -112,6 +60,41 @@ __global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_code_bank(CodeBankPara
   const float sc = p.scale;
   auto emit = [&](int k, float2 v) { D[k] = make_float2(v.x * sc, -v.y * sc); };
   FFT::run(sm, sm_tw, load, emit);
+}
+
+// 2^15-point code spectra: block h transforms the even (h = 0) or odd chips
+// into its half of D (decimation in time), then k_code_bank_combine forms
+// D[k] = conj(E[k] + W^k O[k]) / M and D[k + M/2] = conj(E[k] - W^k O[k]) / M.
+template <int LOGH>
+__global__ void __launch_bounds__((1 << LOGH) >> kLogE) k_code_bank_half(CodeBankParams p) {
+  using FFT = BlockFFT<LOGH, kLogE, -1>;
+  constexpr int H = 1 << LOGH;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  load_tables<LOGH>(sm_tw, p.tw);
+  __syncthreads();
+  const int c = blockIdx.x, h = blockIdx.y;
+  const int8_t* ch = p.chips + p.chip_off[c];
+  const int nc = p.n_chips[c];
+  float2* D = p.D + (int64_t)c * (2 * H) + h * H;
+  auto load = [&](int i) { return make_float2(2 * i + h < nc ? (float)ch[2 * i + h] : 0.f, 0.f); };
+  auto emit = [&](int k, float2 v) { D[k] = v; };
+  FFT::run(sm, sm_tw, load, emit);
+}
+
+__global__ void k_code_bank_combine(float2* D, int H, int n_codes, float scale) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)H * n_codes) return;
+  const int c = (int)(i / H), k = (int)(i % H);
+  float2* Dc = D + (int64_t)c * (2 * H);
+  double sn, cs;
+  sincospi(-(double)k / (double)H, &sn, &cs);  // W^k, W = exp(-2 pi i / 2H)
+  const float2 w = make_float2((float)cs, (float)sn);
+  const float2 e = Dc[k];
+  const float2 o = cmul(w, Dc[k + H]);
+  Dc[k] = make_float2((e.x + o.x) * scale, -(e.y + o.y) * scale);
+  Dc[k + H] = make_float2((e.x - o.x) * scale, -(e.y - o.y) * scale);
 }
 
 // ---------------------------------------------------------------------------
@@ -180,74 +163,6 @@ __global__ void __launch_bounds__(kMixQ) k_mix(MixParams p) {
       const float2 acc = cadd(a0, cmul(a1, wrap));
       Bk[(int64_t)rho * p.M] = cmul(acc, outer);
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// window FFT: G = FFT_M(B), in place
-// ---------------------------------------------------------------------------
-
-template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_window_fft(WindowFftParams p) {
-  using FFT = BlockFFT<LOGM, kLogE, -1>;
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  float2* sm_tw = sm + FFT::SMEM_ELEMS;
-  load_tables<LOGM>(sm_tw, p.tw);
-  __syncthreads();
-  // every input value is read into registers/shared memory before the first
-  // output is written (the passes are separated by block barriers), so the
-  // transform can overwrite its own input row
-  float2* G = p.G + (((int64_t)blockIdx.z * p.K + blockIdx.y) * p.sps + blockIdx.x) * FFT::M;
-  auto load = [&](int i) { return G[i]; };
-  auto emit = [&](int i, float2 v) { G[i] = v; };
-  FFT::run(sm, sm_tw, load, emit);
-}
-
-// ---------------------------------------------------------------------------
-// per-code correlation: G * D -> IFFT -> |.|^2 -> floor sum, argmax
-// ---------------------------------------------------------------------------
-
-template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) >> kLogE) k_corr(CorrParams p) {
-  using FFT = BlockFFT<LOGM, kLogE, +1>;
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  float2* sm_tw = sm + FFT::SMEM_ELEMS;
-  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N);
-
-  const int rho = blockIdx.x, k = blockIdx.y;
-  const int wl = blockIdx.z / p.Cg, c = blockIdx.z % p.Cg;
-  const int w = p.w0 + wl;
-  const int sps = p.sps;
-  load_tables<LOGM>(sm_tw, p.tw);
-  __syncthreads();
-
-  // valid lags of this window (Section 2.1 overlap rule): [0, hop) before the
-  // last window, [0, min(hop, S - L - w*hop)] in the last.
-  int nvalid = p.hop;
-  if (w == p.W - 1) {
-    const int64_t lim = p.S - p.L - (int64_t)w * p.hop;
-    nvalid = (int)(lim < p.hop ? lim : p.hop) + 1;
-  }
-
-  const float2* G = p.G + (((int64_t)wl * p.K + k) * sps + rho) * FFT::M;
-  const float2* D = p.D + (int64_t)c * FFT::M;
-  auto load = [&](int i) { return cmul(G[i], D[i]); };
-  // lag tau = sps*q + rho is valid iff q < qlim
-  const int qlim = (nvalid - rho + sps - 1) / sps;
-  float sum = 0.f, best = -1.f;
-  int bq = 0x7fffffff;
-  auto emit = [&](int q, float2 v) {
-    const float P = fmaf(v.x, v.x, v.y * v.y);
-    sum += P;
-    if (q < qlim) better(best, bq, P, q);
-  };
-  FFT::run(sm, sm_tw, load, emit);
-  int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
-  block_reduce_stats(sum, best, bt, red);
-  if (threadIdx.x == 0) {
-    p.part[(((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho] = make_float4(sum, best, __int_as_float(bt), 0.f);
   }
 }
 
@@ -438,48 +353,43 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams p) {
 // ---------------------------------------------------------------------------
 
 template <int LOGM>
-constexpr int fft_threads() { return (1 << LOGM) >> kLogE; }
-template <int LOGM>
-constexpr size_t fft_smem() {
-  return sizeof(float2) * (BlockFFT<LOGM, kLogE, -1>::SMEM_ELEMS + TwTables<LOGM>::N) + 16 * sizeof(float4) +
-         sizeof(float2) * (kMaxSps + 1);
-}
-
-template <int LOGM>
-static cudaError_t prepare_one() {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_code_bank<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fft_smem<LOGM>())) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_window_fft<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fft_smem<LOGM>())) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(k_corr<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGM>());
+static cudaError_t prepare_code_bank() {
+  return cudaFuncSetAttribute(k_code_bank<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fft_smem<LOGM>());
 }
 
 cudaError_t prepare_kernels() {
   cudaError_t e;
-  if ((e = prepare_one<10>()) != cudaSuccess) return e;
-  if ((e = prepare_one<11>()) != cudaSuccess) return e;
-  if ((e = prepare_one<12>()) != cudaSuccess) return e;
-  if ((e = prepare_one<13>()) != cudaSuccess) return e;
-  return prepare_one<14>();
+  if ((e = prepare_code_bank<10>()) != cudaSuccess) return e;
+  if ((e = prepare_code_bank<11>()) != cudaSuccess) return e;
+  if ((e = prepare_code_bank<12>()) != cudaSuccess) return e;
+  if ((e = prepare_code_bank<13>()) != cudaSuccess) return e;
+  if ((e = prepare_code_bank<14>()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_code_bank_half<14>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fft_smem<14>())) != cudaSuccess)
+    return e;
+  if ((e = prepare_fft_e4()) != cudaSuccess) return e;
+  return prepare_fft_e5();
 }
 
-#define ATLAS_DISPATCH_LOGM(logM, CALL) \
-  switch (logM) {                       \
-    case 10: CALL(10); break;           \
-    case 11: CALL(11); break;           \
-    case 12: CALL(12); break;           \
-    case 13: CALL(13); break;           \
-    case 14: CALL(14); break;           \
-    default: return cudaErrorInvalidValue; \
-  }
-
 cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cudaStream_t s) {
-#define CALL(LM) k_code_bank<LM><<<n_codes, fft_threads<LM>(), fft_smem<LM>(), s>>>(p)
-  ATLAS_DISPATCH_LOGM(logM, CALL)
-#undef CALL
+  switch (logM) {
+    case 10: k_code_bank<10><<<n_codes, fft_threads<10, kLogE>(), fft_smem<10>(), s>>>(p); break;
+    case 11: k_code_bank<11><<<n_codes, fft_threads<11, kLogE>(), fft_smem<11>(), s>>>(p); break;
+    case 12: k_code_bank<12><<<n_codes, fft_threads<12, kLogE>(), fft_smem<12>(), s>>>(p); break;
+    case 13: k_code_bank<13><<<n_codes, fft_threads<13, kLogE>(), fft_smem<13>(), s>>>(p); break;
+    case 14: k_code_bank<14><<<n_codes, fft_threads<14, kLogE>(), fft_smem<14>(), s>>>(p); break;
+    case 15: {
+      k_code_bank_half<14><<<dim3(n_codes, 2), fft_threads<14, kLogE>(), fft_smem<14>(), s>>>(p);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      const int H = 1 << 14;
+      const int64_t n = (int64_t)H * n_codes;
+      k_code_bank_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.D, H, n_codes, p.scale);
+      break;
+    }
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -496,20 +406,12 @@ cudaError_t launch_mix(const MixParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_window_fft(int logM, const WindowFftParams& p, cudaStream_t s) {
-  dim3 grid(p.sps, p.K, p.nw);
-#define CALL(LM) k_window_fft<LM><<<grid, fft_threads<LM>(), fft_smem<LM>(), s>>>(p)
-  ATLAS_DISPATCH_LOGM(logM, CALL)
-#undef CALL
-  return cudaGetLastError();
+cudaError_t launch_window_fft(int logM, int loge, const WindowFftParams& p, cudaStream_t s) {
+  return loge == 4 ? launch_window_fft_e4(logM, p, s) : launch_window_fft_e5(logM, p, s);
 }
 
-cudaError_t launch_corr(int logM, const CorrParams& p, cudaStream_t s) {
-  dim3 grid(p.sps, p.K, p.nw * p.Cg);
-#define CALL(LM) k_corr<LM><<<grid, fft_threads<LM>(), fft_smem<LM>(), s>>>(p)
-  ATLAS_DISPATCH_LOGM(logM, CALL)
-#undef CALL
-  return cudaGetLastError();
+cudaError_t launch_corr(int logM, int loge, const CorrParams& p, cudaStream_t s) {
+  return loge == 4 ? launch_corr_e4(logM, p, s) : launch_corr_e5(logM, p, s);
 }
 
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s) {

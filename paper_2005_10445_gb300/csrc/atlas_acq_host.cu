@@ -28,10 +28,15 @@ namespace {
 // spectra; each such group is searched by one launch sequence.
 struct Group {
   int n_chips = 0, L = 0, N = 0, M = 0, logM = 0, hop = 0;
+  bool split = false;          // M = 2^15: two-block transforms
+  int loge = 5;                // log2 of complex values per thread in the transform kernels
+  int wc = 0;                  // windows per launch group (0 = the context default)
   std::vector<int> codes;      // global code ids
   int* d_codes = nullptr;      // [Cg]
   float2* d_spec = nullptr;    // [Cg][M] conj(FFT_M(chips)) / M
-  const float2* d_tw = nullptr;
+  const float2* d_tw = nullptr;   // tables of the block transform (2^14 when split)
+  const float2* d_tw2 = nullptr;  // tables of M (split only)
+  int parts() const { return split ? 2 : 1; }  // partial results per (cell, rho)
   int windows(int64_t S) const {
     if (S <= N) return 1;
     return (int)((S - N + hop - 1) / hop) + 1;
@@ -190,6 +195,9 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
       g.logM = ilog2(g.M);
       if (g.logM < atlas::kMinLogM || g.logM > atlas::kMaxLogM) return ATLAS_ERR_UNSUPPORTED;
       g.hop = g.N - g.L;
+      g.split = (g.logM == 15);
+      if (o.tile_log2 == 4 || o.tile_log2 == 5) g.loge = o.tile_log2;
+      else if (o.tile_log2 != 0) return ATLAS_ERR_INVALID_ARG;
       by_len[nc] = (int)ctx->groups.size();
       ctx->groups.push_back(g);
       it = by_len.find(nc);
@@ -221,7 +229,7 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   size_t max_part_per_win = 0;
   for (auto& g : ctx->groups) {
     max_win_bytes = std::max(max_win_bytes, (size_t)n_freq * g.N * sizeof(float2));
-    max_part_per_win = std::max(max_part_per_win, (size_t)g.codes.size() * n_freq * sps);
+    max_part_per_win = std::max(max_part_per_win, (size_t)g.codes.size() * n_freq * sps * g.parts());
   }
   int wc = o.windows_per_launch > 0 ? o.windows_per_launch : (int)std::max<size_t>(1, budget / max_win_bytes);
   wc = std::min(wc, 64);
@@ -232,14 +240,20 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   if (cudaMalloc((void**)&ctx->d_part, ctx->part_elems * sizeof(float4)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
 
   // twiddle tables and code banks
-  for (auto& g : ctx->groups) {
-    if (!ctx->d_tw.count(g.logM)) {
-      std::vector<float2> t = twiddle_tables(g.logM);
+  auto tables = [&](int lm, const float2** dst) -> int {
+    if (!ctx->d_tw.count(lm)) {
+      std::vector<float2> t = twiddle_tables(lm);
       float2* d = nullptr;
       CK(upload(&d, t.data(), t.size()));
-      ctx->d_tw[g.logM] = d;
+      ctx->d_tw[lm] = d;
     }
-    g.d_tw = ctx->d_tw[g.logM];
+    *dst = ctx->d_tw[lm];
+    return ATLAS_OK;
+  };
+  for (auto& g : ctx->groups) {
+    int st = tables(g.split ? g.logM - 1 : g.logM, &g.d_tw);
+    if (st != ATLAS_OK) return st;
+    if (g.split && (st = tables(g.logM, &g.d_tw2)) != ATLAS_OK) return st;
     CK(upload(&g.d_codes, g.codes.data(), g.codes.size()));
     if (cudaMalloc((void**)&g.d_spec, sizeof(float2) * (size_t)g.M * g.codes.size()) != cudaSuccess)
       return ATLAS_ERR_NO_MEMORY;
@@ -281,7 +295,8 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
   for (auto& g : ctx->groups) {
     const int W = g.windows(S);
     const int Cg = (int)g.codes.size();
-    const int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
+    int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
+    if (g.wc > 0) wc = std::min(wc, g.wc);
     for (int w0 = 0; w0 < W; w0 += wc) {
       const int nw = std::min(wc, W - w0);
       atlas::MixParams m;
@@ -304,12 +319,13 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       a.nw = nw;
       a.tw = g.d_tw;
       a.G = ctx->d_G;
-      CK(atlas::launch_window_fft(g.logM, a, st));
+      CK(atlas::launch_window_fft(g.logM, g.loge, a, st));
       if (ctx->profiling) ctx->prof_launches += 2;
       CorrParams b;
       b.G = ctx->d_G;
       b.D = g.d_spec;
       b.tw = g.d_tw;
+      b.tw2 = g.d_tw2;
       b.part = ctx->d_part;
       b.S = S;
       b.N = g.N;
@@ -325,7 +341,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       b.status = ctx->d_status;
       const bool timed = ctx->profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
       if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
-      CK(atlas::launch_corr(g.logM, b, st));
+      CK(atlas::launch_corr(g.logM, g.loge, b, st));
       if (timed) {
         CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st));
         ctx->ev_used += 1;
@@ -341,7 +357,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       c.Cg = Cg;
       c.C = ctx->C;
       c.K = ctx->K;
-      c.sps = ctx->sps;
+      c.sps = ctx->sps * g.parts();
       c.N = g.N;
       c.W = W;
       c.w0 = w0;
@@ -391,6 +407,7 @@ void atlas_acq_default_opts(atlas_acq_opts* o) {
   o->threshold = 25.f;
   o->fft_len = 0;
   o->windows_per_launch = 0;
+  o->tile_log2 = 0;
 }
 
 int atlas_acq_create(atlas_acq_t* out, const int8_t* chips, const int32_t* chips_per_code, int32_t n_codes,

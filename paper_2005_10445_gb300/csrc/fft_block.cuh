@@ -84,12 +84,7 @@ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(
 
 template <int DIR, int LEN, int K>
 __device__ __forceinline__ void bfly(float2& a, float2& b) {
-  float2 t;
-  if constexpr (K == 0) {
-    t = b;
-  } else if constexpr (4 * K == LEN) {
-    t = (DIR < 0) ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);  // b * (-/+ i)
-  } else {
+  if constexpr (K != 0 && 4 * K != LEN) {
     // a + w b by four fused multiply-adds, then a - w b = 2a - (a + w b) by two more
     constexpr float wr = Tw<K, LEN, DIR>::re;
     constexpr float wi = Tw<K, LEN, DIR>::im;
@@ -97,10 +92,12 @@ __device__ __forceinline__ void bfly(float2& a, float2& b) {
     const float py = fmaf(b.x, wi, fmaf(b.y, wr, a.y));
     b = make_float2(fmaf(2.f, a.x, -px), fmaf(2.f, a.y, -py));
     a = make_float2(px, py);
-    return;
+  } else {
+    // w = 1, or w = -/+ i (a swap of the parts)
+    const float2 t = (K == 0) ? b : ((DIR < 0) ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x));
+    b = make_float2(a.x - t.x, a.y - t.y);
+    a = make_float2(a.x + t.x, a.y + t.y);
   }
-  b = make_float2(a.x - t.x, a.y - t.y);
-  a = make_float2(a.x + t.x, a.y + t.y);
 }
 
 template <int R, int DIR, int LEN, int... Ks>
@@ -172,12 +169,12 @@ struct BlockFFT {
     constexpr int S = E / R;        // sub-transforms per thread
     constexpr int STRIDE = M / R;   // input stride (a multiple of 32)
     static_assert(STRIDE % 32 == 0 && T % 32 == 0, "padding arithmetic needs 32-multiples");
-    static_assert(D == 0 || D >= 5, "output strides below 32 are not used with 32 values per thread");
     // padded shared index spad(i) = i + i/32 of every access below is a
-    // per-thread base plus a compile-time offset
+    // per-thread base plus a compile-time offset (outputs with 0 < D < 5 excepted)
     constexpr int PSTRIDE = STRIDE + STRIDE / 32;
     constexpr int PT = T + T / 32;
-    constexpr int POUT = D == 0 ? 1 : (1 << D) + (1 << (D - 5));
+    constexpr bool OUT_CLOSED = (D == 0 || D >= 5);
+    constexpr int POUT = D == 0 ? 1 : (D >= 5 ? (1 << D) + (1 << (D - 5)) : 0);
     const int t = threadIdx.x;
     float2 v[E];
     if constexpr (FIRST) {
@@ -214,28 +211,39 @@ struct BlockFFT {
       if constexpr (LAST) {
 #pragma unroll
         for (int r = 0; r < R; ++r) emit(ob + (r << D), v[s * R + r]);
-      } else {
+      } else if constexpr (OUT_CLOSED) {
         float2* dst = sm + spad(ob);
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[r * POUT] = v[s * R + r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[spad(ob + (r << D))] = v[s * R + r];
       }
     }
     if constexpr (!LAST) __syncthreads();
   }
 
-  template <int D, class Load, class Emit>
-  __device__ __forceinline__ static void passes_from(float2* sm, const float2* tw, Load& load, Emit& emit) {
+  template <int D, class Load, class Emit, class Hook>
+  __device__ __forceinline__ static void passes_from(float2* sm, const float2* tw, Load& load, Emit& emit,
+                                                     Hook& hook) {
     constexpr int RB = (LOGM - D) < LOGE ? (LOGM - D) : LOGE;
     constexpr bool LAST = (D + RB == LOGM);
     pass<D, RB, D == 0, LAST>(sm, tw, load, emit);
-    if constexpr (!LAST) passes_from<D + RB>(sm, tw, load, emit);
+    if constexpr (D == 0) hook();
+    if constexpr (!LAST) passes_from<D + RB>(sm, tw, load, emit, hook);
   }
 
   // Full transform: x[i] = load(i) for i < M; emit(k, X[k]) for k < M, unnormalised,
-  // X[k] = sum_i x[i] exp(DIR * 2 pi i * i k / M).
+  // X[k] = sum_i x[i] exp(DIR * 2 pi i * i k / M).  hook() runs once every input
+  // has been read (after the first pass), before any output is emitted.
+  template <class Load, class Emit, class Hook>
+  __device__ __forceinline__ static void run(float2* sm, const float2* tw, Load& load, Emit& emit, Hook& hook) {
+    passes_from<0>(sm, tw, load, emit, hook);
+  }
   template <class Load, class Emit>
   __device__ __forceinline__ static void run(float2* sm, const float2* tw, Load& load, Emit& emit) {
-    passes_from<0>(sm, tw, load, emit);
+    auto none = [] {};
+    passes_from<0>(sm, tw, load, emit, none);
   }
 };
 

@@ -106,22 +106,27 @@ def test_small_parity_all_cells(torch_cuda, seed):
     (5000, 2, 32768),    # M = 2^14
     (8192, 8, 131072),   # M = 2^14, sps 8 (the realistic code shape)
     (600, 16, 16384),    # M = 2^10, sps 16
+    (16384, 2, 65536),   # M = 2^15: split (two-block) transforms
+    (9000, 4, 131072),   # M = 2^15, sps 4
 ])
 def test_sizes_parity(torch_cuda, n_chips, sps, N):
+    """Every transform size and both tile shapes (16 and 32 values per thread)
+    against the oracle, cell by cell."""
     L = n_chips * sps
     S = 2 * N + 3 * (N - L) // 2 + 17   # ragged last window
     wl = synth.realistic(seed=n_chips + sps, seconds=S / 4e6, n_codes=2, n_chips=n_chips, sps=sps,
                          fs_hz=4e6, n_tags=2, snr_range=(-8.0, -2.0),
                          freqs_hz=np.array([-2500.0, 0.0, 2500.0]), min_same_code_gap=2 * N, fft_len=N)
-    s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True)
     ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len)
-    assert n == len(ora)
-    compare_detections(dets, ora)
-    W = cells.shape[0]
-    pairs = [(w, c) for w in range(W) for c in range(2)]
-    if N >= 65536:
-        pairs = pairs[:2] + pairs[-2:]
-    compare_cells(torch_cuda, wl, cells, pairs)
+    for tile in (5, 4):
+        s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True, tile_log2=tile)
+        assert n == len(ora)
+        compare_detections(dets, ora)
+        W = cells.shape[0]
+        pairs = [(w, c) for w in range(W) for c in range(2)]
+        if N >= 65536:
+            pairs = pairs[:2] + pairs[-2:]
+        compare_cells(torch_cuda, wl, cells, pairs)
 
 
 def test_stream_of_exactly_one_code(torch_cuda):
