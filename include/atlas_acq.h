@@ -147,6 +147,52 @@ int atlas_acq_run_cells(atlas_acq_t ctx, void* stream, const float* d_iq, int64_
 int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t n_samples,
                        atlas_detection* h_out, int32_t capacity, int32_t* h_count);
 
+/*
+ * Autotune the transform tile shape (16 or 32 complex values per thread) and
+ * the windows per launch group of every code-length group of the context, by
+ * timing each candidate on the caller's stream over the given device samples
+ * (Section 4.2 plans FFTs for fixed sizes; this plans our own kernels).  With
+ * cache_path (a JSON-lines file, one object per tuned shape keyed by GPU name,
+ * N, M, samples/chip, bins and codes) cached choices are applied without
+ * timing and new ones appended; NULL = no cache.  Allocates a few temporary
+ * buffers; synchronises the stream.  Results of later runs do not depend on
+ * the choice beyond FP32 rounding.
+ */
+int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t n_samples,
+                       const char* cache_path);
+
+/* The tile shape (log2 of values per thread) and windows per launch group in
+ * use for the group of code `code`. */
+int atlas_acq_tuning(atlas_acq_t ctx, int32_t code, int32_t* tile_log2, int32_t* windows_per_launch);
+
+/*
+ * Batched search over many receiver streams (Section 4.3 batches many
+ * correlations per call).  Each stream i has its own context ctxs[i] (codes,
+ * samples/chip, sample rate, frequency grid; contexts must be distinct because
+ * each owns its workspace) and its own device samples d_iq[i] of n_samples[i].
+ * The whole batch -- every stream's launch sequence on its own branch -- is
+ * captured once into a CUDA graph bound to these buffers (Section 4.2: plans
+ * refer to fixed arrays); atlas_acq_batch_run launches that graph.
+ *   d_out    device, [n_streams][capacity] atlas_detection, caller-owned
+ *   d_count  device, [n_streams] int32, caller-owned; count of stream i
+ * The contexts' tuning (atlas_acq_autotune) is frozen into the graph at
+ * creation.  A context must not run other searches while a graph that uses it
+ * executes.  Results equal those of atlas_acq_run on each stream.
+ */
+typedef struct atlas_acq_batch* atlas_acq_batch_t;
+int atlas_acq_batch_create(atlas_acq_batch_t* out, const atlas_acq_t* ctxs, int32_t n_streams,
+                           const float* const* d_iq, const int64_t* n_samples, atlas_detection* d_out,
+                           int32_t capacity, int32_t* d_count);
+
+/* Launch the batch's graph on `stream` (asynchronous). */
+int atlas_acq_batch_run(atlas_acq_batch_t batch, void* stream);
+
+/* Number of kernel launches in one run of the batch's graph. */
+int64_t atlas_acq_batch_kernels(atlas_acq_batch_t batch);
+
+/* Release the graph, its streams and events.  NULL is a no-op. */
+void atlas_acq_batch_destroy(atlas_acq_batch_t batch);
+
 /* Kernel timing collected by the library between atlas_acq_profile_begin and
  * atlas_acq_profile_end. */
 typedef struct {

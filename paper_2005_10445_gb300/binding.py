@@ -30,7 +30,8 @@ EXPORTED = [
     "atlas_acq_default_opts", "atlas_acq_create", "atlas_acq_windows", "atlas_acq_run",
     "atlas_acq_run_cells", "atlas_acq_run_host", "atlas_acq_last_device_status",
     "atlas_acq_last_error", "atlas_acq_destroy", "atlas_acq_strerror", "atlas_acq_profile_begin",
-    "atlas_acq_profile_end", "atlas_acq_run_static",
+    "atlas_acq_profile_end", "atlas_acq_run_static", "atlas_acq_autotune", "atlas_acq_tuning",
+    "atlas_acq_batch_create", "atlas_acq_batch_run", "atlas_acq_batch_kernels", "atlas_acq_batch_destroy",
 ]
 
 
@@ -105,6 +106,18 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_acq_profile_end.restype = ctypes.c_int
     lib.atlas_acq_run_static.argtypes = [vp, vp, i64, vp, i32, i32, f64, vp, i32, i32, ctypes.c_float, vp, i32, vp]
     lib.atlas_acq_run_static.restype = ctypes.c_int
+    lib.atlas_acq_autotune.argtypes = [vp, vp, vp, i64, ctypes.c_char_p]
+    lib.atlas_acq_autotune.restype = ctypes.c_int
+    lib.atlas_acq_tuning.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.atlas_acq_tuning.restype = ctypes.c_int
+    lib.atlas_acq_batch_create.argtypes = [ctypes.POINTER(vp), vp, i32, vp, vp, vp, i32, vp]
+    lib.atlas_acq_batch_create.restype = ctypes.c_int
+    lib.atlas_acq_batch_run.argtypes = [vp, vp]
+    lib.atlas_acq_batch_run.restype = ctypes.c_int
+    lib.atlas_acq_batch_kernels.argtypes = [vp]
+    lib.atlas_acq_batch_kernels.restype = i64
+    lib.atlas_acq_batch_destroy.argtypes = [vp]
+    lib.atlas_acq_batch_destroy.restype = None
     lib.atlas_acq_strerror.argtypes = [ctypes.c_int]
     lib.atlas_acq_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -196,6 +209,15 @@ class Search:
         _check(self._lib.atlas_acq_profile_end(self.ctx, ctypes.byref(p)), self.ctx)
         return {f: getattr(p, f) for f, _ in Profile._fields_}
 
+    def autotune(self, stream: int, d_iq: int, n_samples: int, cache_path: Optional[str] = None) -> None:
+        _check(self._lib.atlas_acq_autotune(self.ctx, stream, d_iq, n_samples,
+                                            cache_path.encode() if cache_path else None), self.ctx)
+
+    def tuning(self, code: int = 0):
+        t, w = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.atlas_acq_tuning(self.ctx, code, ctypes.byref(t), ctypes.byref(w)))
+        return t.value, w.value
+
     def device_status(self) -> int:
         return int(self._lib.atlas_acq_last_device_status(self.ctx))
 
@@ -248,3 +270,41 @@ def run_static_ptr(stream: int, d_iq: int, n_samples: int, d_chips: int, n_chips
     _check(load().atlas_acq_run_static(stream, d_iq, n_samples, d_chips, n_chips, samples_per_chip, float(fs_hz),
                                        fr.ctypes.data, len(fr), fft_len, float(threshold), d_out, capacity,
                                        d_count))
+
+
+class Batch:
+    """atlas_acq_batch_*: one CUDA graph over many streams, each with its own Search."""
+
+    def __init__(self, searches: Sequence["Search"], d_iq_ptrs: Sequence[int], n_samples: Sequence[int],
+                 d_out: int, capacity: int, d_count: int):
+        lib = load()
+        self._lib = lib
+        self.b = ctypes.c_void_p()
+        n = len(searches)
+        self._ctxs = (ctypes.c_void_p * n)(*[s.ctx.value if isinstance(s.ctx, ctypes.c_void_p) else s.ctx
+                                            for s in searches])
+        self._x = (ctypes.c_void_p * n)(*d_iq_ptrs)
+        self._ns = (ctypes.c_int64 * n)(*n_samples)
+        st = lib.atlas_acq_batch_create(ctypes.byref(self.b), ctypes.cast(self._ctxs, ctypes.c_void_p), n,
+                                        ctypes.cast(self._x, ctypes.c_void_p), ctypes.cast(self._ns, ctypes.c_void_p),
+                                        d_out, capacity, d_count)
+        if st != ATLAS_OK:
+            self.b = None
+        _check(st, searches[0].ctx if st == ATLAS_ERR_CUDA else None)
+
+    def run(self, stream: int) -> None:
+        _check(self._lib.atlas_acq_batch_run(self.b, stream))
+
+    def kernels(self) -> int:
+        return int(self._lib.atlas_acq_batch_kernels(self.b))
+
+    def close(self) -> None:
+        if self.b:
+            self._lib.atlas_acq_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

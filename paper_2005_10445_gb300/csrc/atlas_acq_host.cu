@@ -8,7 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <fstream>
 #include <map>
+#include <sstream>
 #include <new>
 #include <string>
 #include <vector>
@@ -224,7 +226,7 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
 
   // windows per launch group: keep the window spectra of one group near L2 size
-  const size_t budget = 64ull << 20;
+  const size_t budget = 128ull << 20;
   size_t max_win_bytes = 0;
   size_t max_part_per_win = 0;
   for (auto& g : ctx->groups) {
@@ -284,15 +286,21 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   return ATLAS_OK;
 }
 
+// only_group >= 0 restricts the search to one code-length group (autotuning).
 int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, atlas_cell* cells,
-             atlas_detection* out, int capacity, int* d_count) {
+             atlas_detection* out, int capacity, int* d_count, int only_group = -1) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cap));
+  const bool profiling = ctx->profiling && cap == cudaStreamCaptureStatusNone;
   CK(cudaMemsetAsync(d_count, 0, sizeof(int), st));
   if (cells) {
     int wmax = 0;
     for (auto& g : ctx->groups) wmax = std::max(wmax, g.windows(S));
     CK(cudaMemsetAsync(cells, 0, sizeof(atlas_cell) * (size_t)wmax * ctx->C * ctx->K, st));
   }
-  for (auto& g : ctx->groups) {
+  for (int gi = 0; gi < (int)ctx->groups.size(); ++gi) {
+    if (only_group >= 0 && gi != only_group) continue;
+    const Group& g = ctx->groups[gi];
     const int W = g.windows(S);
     const int Cg = (int)g.codes.size();
     int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
@@ -320,7 +328,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       a.tw = g.d_tw;
       a.G = ctx->d_G;
       CK(atlas::launch_window_fft(g.logM, g.loge, a, st));
-      if (ctx->profiling) ctx->prof_launches += 2;
+      if (profiling) ctx->prof_launches += 2;
       CorrParams b;
       b.G = ctx->d_G;
       b.D = g.d_spec;
@@ -339,14 +347,14 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       b.K = ctx->K;
       b.Cg = Cg;
       b.status = ctx->d_status;
-      const bool timed = ctx->profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
+      const bool timed = profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
       if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
       CK(atlas::launch_corr(g.logM, g.loge, b, st));
       if (timed) {
         CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st));
         ctx->ev_used += 1;
       }
-      if (ctx->profiling) {
+      if (profiling) {
         ctx->prof_launches += 1;
         ctx->prof_corr_launches += 1;
         ctx->prof_corr_units += (int64_t)nw * Cg * ctx->K;
@@ -368,7 +376,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
       c.count = d_count;
       c.cells = cells;
       CK(atlas::launch_select(c, st));
-      if (ctx->profiling) ctx->prof_launches += 1;
+      if (profiling) ctx->prof_launches += 1;
     }
   }
   if (capacity > 0) {
@@ -385,7 +393,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
     r.capacity = capacity;
     r.count = d_count;
     CK(atlas::launch_refine(r, std::min(capacity, 1024), st));
-    if (ctx->profiling) ctx->prof_launches += 1;
+    if (profiling) ctx->prof_launches += 1;
   }
   return ATLAS_OK;
 }
@@ -504,6 +512,116 @@ int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t
   return ATLAS_OK;
 }
 
+int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t n_samples,
+                       const char* cache_path) {
+  const int a = check_run_args(ctx, d_iq, n_samples, nullptr, 0, d_iq);
+  if (a != ATLAS_OK) return a;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, ctx->device));
+  // cache: one JSON object per line {"key": "...", "tile_log2": t, "windows_per_launch": w, "ms": m}
+  std::map<std::string, std::pair<int, int>> cache;
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      char key[512];
+      int t = 0, w = 0;
+      double ms = 0.0;
+      if (sscanf(line.c_str(), "{\"key\": \"%511[^\"]\", \"tile_log2\": %d, \"windows_per_launch\": %d, \"ms\": %lf}",
+                 key, &t, &w, &ms) == 4 &&
+          (t == 4 || t == 5) && w >= 1)
+        cache[key] = std::make_pair(t, w);
+    }
+  }
+  atlas_detection* d_out = nullptr;
+  int* d_count = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int status = ATLAS_OK;
+  auto fail = [&](cudaError_t e) {
+    ctx->last_error = cudaGetErrorString(e);
+    status = ATLAS_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&d_out, sizeof(atlas_detection) * 64)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&d_count, sizeof(int))) != cudaSuccess || (e = cudaEventCreate(&e0)) != cudaSuccess ||
+      (e = cudaEventCreate(&e1)) != cudaSuccess)
+    fail(e);
+  std::ofstream outf;
+  if (status == ATLAS_OK && cache_path) outf.open(cache_path, std::ios::app);
+  const bool was_profiling = ctx->profiling;
+  ctx->profiling = false;
+  for (int gi = 0; status == ATLAS_OK && gi < (int)ctx->groups.size(); ++gi) {
+    Group& g = ctx->groups[gi];
+    std::ostringstream ks;
+    ks << prop.name << "|N=" << g.N << "|M=" << g.M << "|sps=" << ctx->sps << "|K=" << ctx->K
+       << "|codes=" << g.codes.size();
+    const std::string key = ks.str();
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      g.loge = it->second.first;
+      g.wc = it->second.second;
+      continue;
+    }
+    // time on (at most) the first 32 windows of the group
+    const int64_t S_tune = std::min<int64_t>(n_samples, (int64_t)g.N + 31ll * g.hop);
+    const int W = g.windows(S_tune);
+    const int fit = std::max(1, (int)(ctx->G_elems / ((size_t)ctx->K * g.N)));
+    int best_t = g.loge, best_w = g.wc;
+    double best_ms = 1e30;
+    for (int t : {5, 4}) {
+      for (int w : {1, 2, 4, 8}) {
+        if (w > std::min(fit, ctx->wc_max) || (w > 1 && w >= 2 * W)) continue;
+        g.loge = t;
+        g.wc = w;
+        int r = run_impl(ctx, st, reinterpret_cast<const float2*>(d_iq), S_tune, nullptr, d_out, 64, d_count, gi);
+        if (r != ATLAS_OK) {
+          status = r;
+          break;
+        }
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { fail(e); break; }
+        for (int rep = 0; rep < 2 && status == ATLAS_OK; ++rep)
+          status = run_impl(ctx, st, reinterpret_cast<const float2*>(d_iq), S_tune, nullptr, d_out, 64, d_count, gi);
+        if (status != ATLAS_OK) break;
+        float ms = 0.f;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+          fail(e);
+          break;
+        }
+        if (ms / 2 < best_ms) {
+          best_ms = ms / 2;
+          best_t = t;
+          best_w = w;
+        }
+      }
+      if (status != ATLAS_OK) break;
+    }
+    g.loge = best_t;
+    g.wc = best_w;
+    if (status == ATLAS_OK && outf.is_open())
+      outf << "{\"key\": \"" << key << "\", \"tile_log2\": " << best_t << ", \"windows_per_launch\": " << best_w
+           << ", \"ms\": " << best_ms << "}\n";
+  }
+  ctx->profiling = was_profiling;
+  cudaFree(d_out);
+  cudaFree(d_count);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return status;
+}
+
+int atlas_acq_tuning(atlas_acq_t ctx, int32_t code, int32_t* tile_log2, int32_t* windows_per_launch) {
+  if (!ctx || code < 0 || code >= ctx->C) return ATLAS_ERR_INVALID_ARG;
+  const Group& g = ctx->groups[ctx->code_group[code]];
+  if (tile_log2) *tile_log2 = g.loge;
+  if (windows_per_launch) {
+    const int fit = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
+    *windows_per_launch = g.wc > 0 ? std::min(g.wc, fit) : fit;
+  }
+  return ATLAS_OK;
+}
+
 int atlas_acq_profile_begin(atlas_acq_t ctx, int32_t max_timed) {
   if (!ctx || max_timed < 0) return ATLAS_ERR_INVALID_ARG;
   for (auto e : ctx->ev) cudaEventDestroy(e);
@@ -560,5 +678,118 @@ const char* atlas_acq_strerror(int status) {
     default: return "unknown status";
   }
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched search: many receiver streams, one CUDA graph
+// ---------------------------------------------------------------------------
+
+struct atlas_acq_batch {
+  int device = 0;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernel_nodes = 0;
+};
+
+namespace {
+void free_batch(atlas_acq_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+}  // namespace
+
+extern "C" {
+
+int atlas_acq_batch_create(atlas_acq_batch_t* out, const atlas_acq_t* ctxs, int32_t n_streams,
+                           const float* const* d_iq, const int64_t* n_samples, atlas_detection* d_out,
+                           int32_t capacity, int32_t* d_count) {
+  if (!out) return ATLAS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ctxs || n_streams <= 0 || !d_iq || !n_samples || !d_count || capacity < 0 || (capacity > 0 && !d_out))
+    return ATLAS_ERR_INVALID_ARG;
+  for (int i = 0; i < n_streams; ++i) {
+    if (!ctxs[i] || !d_iq[i] || n_samples[i] < ctxs[i]->max_L) return ATLAS_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return ATLAS_ERR_INVALID_ARG;  // each stream needs its own workspace
+  }
+  atlas_acq_batch* b = new (std::nothrow) atlas_acq_batch();
+  if (!b) return ATLAS_ERR_NO_MEMORY;
+  atlas_acq_ctx* ctx = ctxs[0];
+  int status = ATLAS_OK;
+  bool capturing = false;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; e == cudaSuccess && i < n_streams; ++i) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t j = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->streams.push_back(s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->joins.push_back(j);
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    capturing = true;
+    e = cudaEventRecord(b->fork, b->origin);
+  }
+  for (int i = 0; e == cudaSuccess && status == ATLAS_OK && i < n_streams; ++i) {
+    e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+    if (e != cudaSuccess) break;
+    status = run_impl(ctxs[i], b->streams[i], reinterpret_cast<const float2*>(d_iq[i]), n_samples[i], nullptr,
+                      d_out ? d_out + (size_t)i * capacity : nullptr, capacity, d_count + i);
+    if (status != ATLAS_OK) {
+      ctx = ctxs[i];
+      break;
+    }
+    e = cudaEventRecord(b->joins[i], b->streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+  }
+  if (capturing) {
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
+    b->graph = g;
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess && status == ATLAS_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e == cudaSuccess && status == ATLAS_OK) {
+    size_t n = 0;
+    e = cudaGraphGetNodes(b->graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n) e = cudaGraphGetNodes(b->graph, nodes.data(), &n);
+    for (size_t k = 0; e == cudaSuccess && k < n; ++k) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(nodes[k], &t);
+      if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) b->kernel_nodes += 1;
+    }
+  }
+  if (e != cudaSuccess) status = fail_cuda(ctx, e);
+  if (status != ATLAS_OK) {
+    free_batch(b);
+    return status;
+  }
+  *out = b;
+  return ATLAS_OK;
+}
+
+int atlas_acq_batch_run(atlas_acq_batch_t b, void* stream) {
+  if (!b || !b->exec) return ATLAS_ERR_INVALID_ARG;
+  return cudaGraphLaunch(b->exec, (cudaStream_t)stream) == cudaSuccess ? ATLAS_OK : ATLAS_ERR_CUDA;
+}
+
+int64_t atlas_acq_batch_kernels(atlas_acq_batch_t b) { return b ? b->kernel_nodes : -1; }
+
+void atlas_acq_batch_destroy(atlas_acq_batch_t b) { free_batch(b); }
 
 }  // extern "C"

@@ -226,3 +226,53 @@ def small(seed: int = 11, S: int = 40000, n_codes: int = 3, n_chips: int = 600, 
     return realistic(seed=seed, seconds=S / fs_hz, n_codes=n_codes, n_chips=n_chips, sps=sps,
                      fs_hz=fs_hz, n_tags=n_tags, snr_range=snr_range, freqs_hz=freqs,
                      sigma=sigma, jitter_hz=20.0, min_same_code_gap=2 * N, fft_len=N)
+
+
+def batch(seed: int = 3, n_streams: int = 8, duration_s=(0.5, 2.0), fs_choices=(2e6, 4e6, 8e6),
+          n_codes: int = 64, chip_choices=(2048, 4096, 8192, 16384), bins=(15, 63), bin_step_hz: float = 500.0,
+          tags_per_group: int = 5, snr_range=(-20.0, 0.0), sigma: float = 2048.0,
+          chip_rate_hz: float = 1e6) -> List[Workload]:
+    """Several receiver streams for one batched search: each stream draws its
+    sample rate from fs_choices (samples/chip = fs / chip rate) and its duration
+    from duration_s, and has its own odd number of bins in [bins], spaced
+    bin_step_hz and centred on 0.  All streams search the same codes, whose
+    lengths are drawn from chip_choices.  About tags_per_group tags per stream
+    and code-length group, with SNR uniform in snr_range, integer delays,
+    on-grid carrier offsets plus a jitter of at most a tenth of a bin step."""
+    rng = np.random.default_rng(seed)
+    lengths = [int(rng.choice(chip_choices)) for _ in range(n_codes)]
+    chips = [random_chips(n, seed * 7_919 + c) for c, n in enumerate(lengths)]
+    out: List[Workload] = []
+    for s in range(n_streams):
+        fs = float(rng.choice(fs_choices))
+        sps = int(round(fs / chip_rate_hz))
+        S = int(round(rng.uniform(*duration_s) * fs))
+        lo, hi = bins
+        K = int(rng.integers(lo // 2, hi // 2 + 1)) * 2 + 1
+        freqs = (np.arange(K, dtype=np.float64) - (K - 1) / 2) * bin_step_hz
+        x = awgn(S, sigma, rng)
+        tags: List[Tag] = []
+        for n_chips in sorted(set(lengths)):
+            group = [c for c in range(n_codes) if lengths[c] == n_chips]
+            L = n_chips * sps
+            if L >= S:
+                continue
+            gap = 4 * (1 << (L - 1).bit_length())
+            placed: dict = {}
+            for _ in range(tags_per_group):
+                for _try in range(100):
+                    c = int(rng.choice(group))
+                    d = int(rng.integers(0, S - L + 1))
+                    if all(abs(d - p) >= gap for p in placed.get(c, [])):
+                        break
+                else:
+                    continue
+                placed.setdefault(c, []).append(d)
+                b = int(rng.integers(0, K))
+                tg = Tag(code=c, delay=float(d), freq_hz=float(freqs[b] + rng.uniform(-0.1, 0.1) * bin_step_hz),
+                         bin=b, snr_db=float(rng.uniform(*snr_range)), phase=float(rng.uniform(0, 2 * math.pi)))
+                inject(x, chips[c], sps, fs, tg, sigma)
+                tags.append(tg)
+        out.append(Workload(f"batch stream {s}: {S} samples at {fs/1e6:g} MS/s, sps {sps}, {K} bins", x, chips,
+                            sps, fs, freqs, 0, tags, sigma))
+    return out

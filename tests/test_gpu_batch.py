@@ -1,0 +1,97 @@
+"""Batched search (many receiver streams in one CUDA graph) and the autotuner,
+against the per-stream entry point and the FP64 oracle (GPU only)."""
+import numpy as np
+import pytest
+
+from oracle import acq
+from paper_2005_10445_gb300 import synth
+
+from test_gpu_parity import compare_detections
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(built_lib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def small_batch():
+    # 3 streams at 2 or 4 MS/s, 5 codes of three lengths (M = 2^11 .. 2^13), 3-7 bins
+    return synth.batch(seed=5, n_streams=3, duration_s=(0.008, 0.012), fs_choices=(2e6, 4e6), n_codes=5,
+                       chip_choices=(600, 1100, 2100), bins=(3, 7), tags_per_group=2, snr_range=(-10.0, -2.0))
+
+
+def test_batch_graph_matches_streams_and_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import DETECTION_DTYPE, Batch, Search
+    wls = small_batch()
+    cap = 256
+    searches = [Search(w.chips, w.sps, w.fs_hz, w.freqs_hz) for w in wls]
+    xs = [torch.from_numpy(w.iq().copy()).cuda() for w in wls]
+    out = torch.zeros(len(wls) * cap * 32, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(len(wls), dtype=torch.int32, device="cuda")
+    b = Batch(searches, [x.data_ptr() for x in xs], [w.n_samples for w in wls], out.data_ptr(), cap, cnt.data_ptr())
+    assert b.kernels() > 0
+    st = torch.cuda.current_stream()
+    results = []
+    for _ in range(2):  # the graph can be replayed
+        out.zero_()
+        b.run(st.cuda_stream)
+        st.synchronize()
+        results.append((out.cpu().numpy().copy(), cnt.cpu().numpy().copy()))
+    assert results[0][0].tobytes() == results[1][0].tobytes() and (results[0][1] == results[1][1]).all()
+    dets_all = results[0][0].view(DETECTION_DTYPE).reshape(len(wls), cap)
+    for i, (w, s, x) in enumerate(zip(wls, searches, xs)):
+        n = int(results[0][1][i])
+        got = dets_all[i, :min(n, cap)]
+        ref, n_ref, _ = s.run(x, capacity=cap)
+        assert n == n_ref and got.tobytes() == ref.tobytes()
+        ora, _ = acq.search(w.x, w.chips, w.sps, w.fs_hz, w.freqs_hz, 0)
+        assert n == len(ora)
+        compare_detections(got, ora)
+        # every injected tag found
+        found = {(int(d["code"]), int(d["window"]), int(d["lag"])) for d in got}
+        for t in w.tags:
+            W, hop, N = s.windows(t.code, w.n_samples)
+            wi = min(int(t.delay) // hop, W - 1)
+            assert (t.code, wi, int(t.delay) - wi * hop) in found
+    b.close()
+
+
+def test_batch_rejects_shared_context(torch_cuda):
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import AtlasError, Batch, Search
+    w = small_batch()[0]
+    s = Search(w.chips, w.sps, w.fs_hz, w.freqs_hz)
+    x = torch.from_numpy(w.iq().copy()).cuda()
+    out = torch.zeros(2 * 16 * 32, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
+    with pytest.raises(AtlasError):
+        Batch([s, s], [x.data_ptr()] * 2, [w.n_samples] * 2, out.data_ptr(), 16, cnt.data_ptr())
+
+
+def test_autotune_choice_cache_and_parity(torch_cuda, tmp_path):
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import Search
+    w = synth.small(seed=12)
+    x = torch.from_numpy(w.iq().copy()).cuda()
+    st = torch.cuda.current_stream()
+    cache = str(tmp_path / "tune.jsonl")
+    s1 = Search(w.chips, w.sps, w.fs_hz, w.freqs_hz, fft_len=w.fft_len)
+    s1.autotune(st.cuda_stream, x.data_ptr(), w.n_samples, cache)
+    t1 = s1.tuning(0)
+    assert t1[0] in (4, 5) and t1[1] >= 1
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) == 1 and '"tile_log2"' in lines[0]
+    s2 = Search(w.chips, w.sps, w.fs_hz, w.freqs_hz, fft_len=w.fft_len)
+    s2.autotune(st.cuda_stream, x.data_ptr(), w.n_samples, cache)   # from the cache
+    assert s2.tuning(0) == t1
+    assert len(open(cache).read().strip().splitlines()) == 1
+    dets, n, _ = s2.run(x)
+    ora, _ = acq.search(w.x, w.chips, w.sps, w.fs_hz, w.freqs_hz, w.fft_len)
+    assert n == len(ora)
+    compare_detections(dets, ora)
