@@ -259,7 +259,7 @@ def run_batching(args, rank: int, world: int, dev, torch, dist) -> None:
             "roofline": {"bound": "alu", "achieved": step_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": step_tflops / FP32_PEAK_TFLOPS, "traffic": None,
                          "kernel": "whole graph (executed polyphase flops / step time)",
-                         "k_corr_share_outside_graph": corr_ms / max(1e-9, corr_ms), "k_corr_launches": corr_launches,
+                         "k_corr_ms_per_step_outside_graph": corr_ms, "k_corr_launches": corr_launches,
                          "k_corr_cells": corr_units},
             "gpu_launches": b.kernels() * args.steps,
             "clocks": clocks,
