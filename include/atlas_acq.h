@@ -193,6 +193,74 @@ int64_t atlas_acq_batch_kernels(atlas_acq_batch_t batch);
 /* Release the graph, its streams and events.  NULL is a no-op. */
 void atlas_acq_batch_destroy(atlas_acq_batch_t batch);
 
+/* ------------------------------------------------------------------------
+ * Learned (code, bin) proposal.  The paper has no learned component; the
+ * proposal prunes its exhaustive search (every code correlated in every
+ * block, Sections 2.1 and 3): a small network looks at a window's Welch power
+ * spectrum (segments of 4096 samples, Hann taper, log10, mean removed) and
+ * ranks (code, bin) candidates; only the top-k are correlated, and windows
+ * where it is not confident fall back to the exhaustive search, which also
+ * labels the training data.
+ * Network: conv1d (8 channels, kernel 16, stride 8) + ReLU, dense 4096 -> 48
+ * + ReLU, heads: code logits [n_codes], bin logits [n_bins], presence logit.
+ * Parameters: one FP32 array in the order conv_w [8][16], conv_b [8],
+ * w1 [4096][48], b1 [48], wc [48][n_codes], bc [n_codes], wb [48][n_bins],
+ * bb [n_bins], wp [48], bp [1]; inference uses an FP16 copy (FP32 accumulate).
+ * ------------------------------------------------------------------------ */
+typedef struct atlas_prop* atlas_prop_t;
+
+/* Create a network with seeded He-uniform weights (1 <= n_codes, n_bins <= 256). */
+int atlas_prop_create(atlas_prop_t* out, int32_t n_codes, int32_t n_bins, uint64_t seed);
+int64_t atlas_prop_num_params(atlas_prop_t p);
+/* Copy the FP32 parameters out to / in from host memory (set resets Adam). */
+int atlas_prop_get_params(atlas_prop_t p, float* h_params);
+int atlas_prop_set_params(atlas_prop_t p, const float* h_params);
+
+/* Features of n_windows windows of window_len samples (a multiple of 4096) starting at
+ * first_sample + w * stride of the device stream d_iq [n_samples][2]; samples outside
+ * the stream read as zero.  d_feat: device [n_windows][4096]. */
+int atlas_prop_features(atlas_prop_t p, void* stream, const float* d_iq, int64_t n_samples, int64_t first_sample,
+                        int64_t stride, int32_t window_len, int32_t n_windows, float* d_feat);
+
+/* Mean loss over the batch into *d_loss (device float) and the gradient of every
+ * parameter into d_grad (device, [num_params]; NULL = the network's own buffer).
+ * d_code / d_bin: device [batch] labels, code < 0 for a window without a detection. */
+int atlas_prop_loss_grad(atlas_prop_t p, void* stream, const float* d_feat, const int32_t* d_code,
+                         const int32_t* d_bin, int32_t batch, float* d_loss, float* d_grad);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) with the given gradient
+ * (NULL = the network's own buffer); refreshes the FP16 copy. */
+int atlas_prop_adam(atlas_prop_t p, void* stream, const float* d_grad, float lr);
+
+/* Logits of a batch (any pointer may be NULL): FP16 weights when half_weights != 0. */
+int atlas_prop_logits(atlas_prop_t p, void* stream, const float* d_feat, int32_t batch, int32_t half_weights,
+                      float* d_zc, float* d_zb, float* d_zp);
+
+/* Top-k (code, bin) candidates per window by log p(code) + log p(bin) (ties to the
+ * smaller code*n_bins + bin), FP16 weights.  d_cand: [n_windows][topk][2] int32
+ * (code, bin); d_conf: [n_windows][2] = {probability of the top pair, presence
+ * probability}.  1 <= topk <= 32. */
+int atlas_prop_candidates(atlas_prop_t p, void* stream, const float* d_feat, int32_t n_windows, int32_t topk,
+                          int32_t* d_cand, float* d_conf);
+
+/*
+ * Search with the proposal: features and candidates for every window of the
+ * context's single code length; each window whose top-pair probability is at
+ * least tau_fb is searched only over its top-k (code, bin) candidates (per code,
+ * the best of its candidate bins), every other window by the exhaustive search.
+ * Output as atlas_acq_run (ordered by window, then code; refined ToA).
+ * h_n_fallback (host, may be NULL) receives the number of exhaustive windows.
+ * Synchronous: it reads the candidates on the host to build the work lists, and
+ * grows its workspaces on first use for a given number of windows.  tau_fb = 0
+ * never falls back; tau_fb > 1 always does (the exhaustive search).
+ */
+int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, const float* d_iq,
+                           int64_t n_samples, int32_t topk, float tau_fb, atlas_detection* d_out, int32_t capacity,
+                           int32_t* d_count, int32_t* h_n_fallback);
+
+const char* atlas_prop_last_error(atlas_prop_t p);
+void atlas_prop_destroy(atlas_prop_t p);
+
 /* Kernel timing collected by the library between atlas_acq_profile_begin and
  * atlas_acq_profile_end. */
 typedef struct {

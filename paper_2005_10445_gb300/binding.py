@@ -32,6 +32,9 @@ EXPORTED = [
     "atlas_acq_last_error", "atlas_acq_destroy", "atlas_acq_strerror", "atlas_acq_profile_begin",
     "atlas_acq_profile_end", "atlas_acq_run_static", "atlas_acq_autotune", "atlas_acq_tuning",
     "atlas_acq_batch_create", "atlas_acq_batch_run", "atlas_acq_batch_kernels", "atlas_acq_batch_destroy",
+    "atlas_prop_create", "atlas_prop_num_params", "atlas_prop_get_params", "atlas_prop_set_params",
+    "atlas_prop_features", "atlas_prop_loss_grad", "atlas_prop_adam", "atlas_prop_logits", "atlas_prop_candidates",
+    "atlas_acq_run_proposed", "atlas_prop_last_error", "atlas_prop_destroy",
 ]
 
 
@@ -118,6 +121,31 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_acq_batch_kernels.restype = i64
     lib.atlas_acq_batch_destroy.argtypes = [vp]
     lib.atlas_acq_batch_destroy.restype = None
+    u64, f32 = ctypes.c_uint64, ctypes.c_float
+    lib.atlas_prop_create.argtypes = [ctypes.POINTER(vp), i32, i32, u64]
+    lib.atlas_prop_create.restype = ctypes.c_int
+    lib.atlas_prop_num_params.argtypes = [vp]
+    lib.atlas_prop_num_params.restype = i64
+    lib.atlas_prop_get_params.argtypes = [vp, vp]
+    lib.atlas_prop_get_params.restype = ctypes.c_int
+    lib.atlas_prop_set_params.argtypes = [vp, vp]
+    lib.atlas_prop_set_params.restype = ctypes.c_int
+    lib.atlas_prop_features.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp]
+    lib.atlas_prop_features.restype = ctypes.c_int
+    lib.atlas_prop_loss_grad.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
+    lib.atlas_prop_loss_grad.restype = ctypes.c_int
+    lib.atlas_prop_adam.argtypes = [vp, vp, vp, f32]
+    lib.atlas_prop_adam.restype = ctypes.c_int
+    lib.atlas_prop_logits.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp]
+    lib.atlas_prop_logits.restype = ctypes.c_int
+    lib.atlas_prop_candidates.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    lib.atlas_prop_candidates.restype = ctypes.c_int
+    lib.atlas_acq_run_proposed.argtypes = [vp, vp, vp, vp, i64, i32, f32, vp, i32, vp, ctypes.POINTER(i32)]
+    lib.atlas_acq_run_proposed.restype = ctypes.c_int
+    lib.atlas_prop_last_error.argtypes = [vp]
+    lib.atlas_prop_last_error.restype = ctypes.c_char_p
+    lib.atlas_prop_destroy.argtypes = [vp]
+    lib.atlas_prop_destroy.restype = None
     lib.atlas_acq_strerror.argtypes = [ctypes.c_int]
     lib.atlas_acq_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -308,3 +336,72 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Proposal:
+    """atlas_prop_*: the learned (code, bin) proposal network."""
+
+    def __init__(self, n_codes: int, n_bins: int, seed: int = 0):
+        lib = load()
+        self._lib = lib
+        self.p = ctypes.c_void_p()
+        _check(lib.atlas_prop_create(ctypes.byref(self.p), n_codes, n_bins, seed))
+        self.n_codes, self.n_bins = n_codes, n_bins
+        self.n_params = int(lib.atlas_prop_num_params(self.p))
+
+    def _chk(self, st):
+        if st != ATLAS_OK:
+            msg = strerror(st)
+            if st == ATLAS_ERR_CUDA:
+                msg += ": " + self._lib.atlas_prop_last_error(self.p).decode()
+            raise AtlasError(st, msg)
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        self._chk(self._lib.atlas_prop_get_params(self.p, out.ctypes.data))
+        return out
+
+    def set_params(self, v: np.ndarray) -> None:
+        v = np.ascontiguousarray(v, np.float32)
+        assert v.size == self.n_params
+        self._chk(self._lib.atlas_prop_set_params(self.p, v.ctypes.data))
+
+    def features(self, stream: int, d_iq: int, n_samples: int, first: int, stride: int, window_len: int,
+                 n_windows: int, d_feat: int) -> None:
+        self._chk(self._lib.atlas_prop_features(self.p, stream, d_iq, n_samples, first, stride, window_len,
+                                                n_windows, d_feat))
+
+    def loss_grad(self, stream: int, d_feat: int, d_code: int, d_bin: int, batch: int, d_loss: int,
+                  d_grad: int = 0) -> None:
+        self._chk(self._lib.atlas_prop_loss_grad(self.p, stream, d_feat, d_code, d_bin, batch, d_loss,
+                                                 d_grad or None))
+
+    def adam(self, stream: int, lr: float, d_grad: int = 0) -> None:
+        self._chk(self._lib.atlas_prop_adam(self.p, stream, d_grad or None, lr))
+
+    def logits(self, stream: int, d_feat: int, batch: int, half: bool, d_zc: int, d_zb: int, d_zp: int) -> None:
+        self._chk(self._lib.atlas_prop_logits(self.p, stream, d_feat, batch, 1 if half else 0, d_zc or None,
+                                              d_zb or None, d_zp or None))
+
+    def candidates(self, stream: int, d_feat: int, n_windows: int, topk: int, d_cand: int, d_conf: int) -> None:
+        self._chk(self._lib.atlas_prop_candidates(self.p, stream, d_feat, n_windows, topk, d_cand, d_conf))
+
+    def close(self) -> None:
+        if self.p:
+            self._lib.atlas_prop_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_proposed(search: "Search", prop: Proposal, stream: int, d_iq: int, n_samples: int, topk: int,
+                 tau_fb: float, d_out: int, capacity: int, d_count: int) -> int:
+    """atlas_acq_run_proposed; returns the number of windows that fell back to the exhaustive search."""
+    nfb = ctypes.c_int32(0)
+    _check(load().atlas_acq_run_proposed(search.ctx, prop.p, stream, d_iq, n_samples, topk, float(tau_fb), d_out,
+                                         capacity, d_count, ctypes.byref(nfb)), search.ctx)
+    return nfb.value

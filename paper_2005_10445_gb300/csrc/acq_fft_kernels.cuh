@@ -71,14 +71,27 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
   float2* sm_tw = sm + FFT::SMEM_ELEMS;
   float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + TwTables<LOGM + 1>::N);
 
-  const int rho = blockIdx.x, k = blockIdx.y;
-  const int wl = blockIdx.z / p.Cg, c = blockIdx.z % p.Cg;
-  const int sps = p.sps;
+  const int rho = blockIdx.x, sps = p.sps;
+  int64_t row, out;  // G row and partial-result index of this block
+  int c, w;
+  if (p.pairs) {     // listed (G row, code, window) cells
+    const int4 pr = p.pairs[blockIdx.z];
+    row = (int64_t)pr.x * sps + rho;
+    c = pr.y;
+    w = pr.z;
+    out = (int64_t)blockIdx.z * sps + rho;
+  } else {
+    const int k = blockIdx.y, wl = blockIdx.z / p.Cg;
+    c = blockIdx.z % p.Cg;
+    w = p.w0 + wl;
+    row = ((int64_t)wl * p.K + k) * sps + rho;
+    out = (((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho;
+  }
   load_tables<LOGM>(sm_tw, p.tw);
   __syncthreads();
-  const int nvalid = valid_lags(p, p.w0 + wl);
+  const int nvalid = valid_lags(p, w);
 
-  const float2* G = p.G + (((int64_t)wl * p.K + k) * sps + rho) * FFT::M;
+  const float2* G = p.G + row * FFT::M;
   const float2* D = p.D + (int64_t)c * FFT::M;
   auto load = [&](int i) { return cmul(G[i], D[i]); };
   // lag tau = sps*q + rho is valid iff q < qlim
@@ -93,9 +106,7 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
   FFT::run(sm, sm_tw, load, emit);
   int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
   block_reduce_stats(sum, best, bt, red);
-  if (threadIdx.x == 0) {
-    p.part[(((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho] = make_float4(sum, best, __int_as_float(bt), 0.f);
-  }
+  if (threadIdx.x == 0) p.part[out] = make_float4(sum, best, __int_as_float(bt), 0.f);
 }
 
 template <int LOGH, int LOGE>
@@ -216,7 +227,8 @@ struct FftLaunch {
   }
 
   static cudaError_t corr(int logM, const CorrParams& p, cudaStream_t s) {
-    dim3 grid(p.sps, p.K, p.nw * p.Cg);
+    if (p.pairs && logM > 14) return cudaErrorInvalidValue;  // listed cells: single-block sizes only
+    dim3 grid(p.sps, p.pairs ? 1 : p.K, p.pairs ? p.n_pairs : p.nw * p.Cg);
     switch (logM) {
       case 10: k_corr<10, LOGE><<<grid, fft_threads<10, LOGE>(), fft_smem<10>(), s>>>(p); break;
       case 11: k_corr<11, LOGE><<<grid, fft_threads<11, LOGE>(), fft_smem<11>(), s>>>(p); break;

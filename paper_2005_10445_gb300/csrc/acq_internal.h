@@ -27,6 +27,8 @@ struct MixParams {
   int K;
   const uint64_t* inc;      // [K] phase increment per sample, turns * 2^64 (two's complement)
   float2* B;                // out [nw][K][sps][M]: B_rho[q] = sum_s y[(sps q + rho + s) mod N]
+  const int2* items = nullptr;  // optional (window, bin) list: then B is [n_items][sps][M]
+  int n_items = 0;
 };
 
 // Window FFT: one block per (rho, k, window in the launch group), in place.
@@ -41,12 +43,21 @@ struct CorrParams {
   const float2* G;          // [nw][K][sps][M]
   const float2* D;          // [Cg][M] conj(FFT_M(chips)) / M
   const float2* tw;         // twiddle tables of the block transform
-  const float2* tw2;        // tables of the full size M (split transforms only)
+  const float2* tw2 = nullptr;  // tables of the full size M (split transforms only)
   float4* part;             // out [nw][Cg][K][sps] (x2 for split) = {sum P, P*, tau*, 0}
   int64_t S;
   int N, M, sps, hop, W, L;
   int w0, nw, K, Cg;
   int* status;
+  const int4* pairs = nullptr;  // optional list of (G row, code, window, -): then part is [n_pairs][sps]
+  int n_pairs = 0;
+};
+
+// Per listed cell: combine the sps partial results into {score, P*, lag, floor}.
+struct PairStatsParams {
+  const float4* part;       // [n][sps]
+  int n, sps, N;
+  float4* out;              // [n] = {P* / floor, P*, lag (as int bits), floor}
 };
 
 // Bin selection, threshold and ordered compaction for one launch group.
@@ -99,6 +110,7 @@ cudaError_t launch_window_fft_e5(int logM, const WindowFftParams& p, cudaStream_
 cudaError_t launch_corr_e4(int logM, const CorrParams& p, cudaStream_t s);
 cudaError_t launch_corr_e5(int logM, const CorrParams& p, cudaStream_t s);
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s);
+cudaError_t launch_pair_stats(const PairStatsParams& p, cudaStream_t s);
 cudaError_t launch_refine(const RefineParams& p, int grid, cudaStream_t s);
 cudaError_t prepare_kernels();  // raises the dynamic shared-memory limits once per process
 

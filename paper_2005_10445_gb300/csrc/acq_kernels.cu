@@ -114,10 +114,18 @@ __global__ void __launch_bounds__(kMixQ) k_mix(MixParams p) {
   __shared__ float2 X[SPS * kMixRow];
   __shared__ float2 inner[kMixKG][2 * SPS];
   const int q0 = blockIdx.x * kMixQ;
-  const int k0 = blockIdx.y * kMixKG;
-  const int nk = min(kMixKG, p.K - k0);
   const int wl = blockIdx.z;
-  const int64_t base = (int64_t)(p.w0 + wl) * p.hop;
+  int k0, nk, w;
+  if (p.items) {  // one listed (window, bin) per block row
+    w = p.items[wl].x;
+    k0 = p.items[wl].y;
+    nk = 1;
+  } else {
+    w = p.w0 + wl;
+    k0 = blockIdx.y * kMixKG;
+    nk = min(kMixKG, p.K - k0);
+  }
+  const int64_t base = (int64_t)w * p.hop;
   const int N = p.N;
   for (int i = threadIdx.x; i < SPS * (kMixQ + 1); i += kMixQ) {
     int t = SPS * q0 + i;
@@ -144,7 +152,7 @@ __global__ void __launch_bounds__(kMixQ) k_mix(MixParams p) {
     const int k = k0 + kk;
     const float2 outer = expi_neg(p.inc[k] * (uint64_t)SPS * (uint64_t)q);
     const float2 wrap = last ? inner[kk][2 * SPS - 1] : make_float2(1.f, 0.f);
-    float2* Bk = p.B + (((int64_t)wl * p.K + k) * SPS) * p.M + q;
+    float2* Bk = p.B + (p.items ? (int64_t)wl * SPS : ((int64_t)wl * p.K + k) * SPS) * p.M + q;
 #pragma unroll
     for (int rho = 0; rho < SPS; ++rho) {
       float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
@@ -254,6 +262,20 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(SelectParams p) {
     __syncthreads();
   }
   if (threadIdx.x == 0) *p.count = base_sh;
+}
+
+__global__ void k_pair_stats(PairStatsParams p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  float sum = 0.f, best = -1.f;
+  int bt = 0x7fffffff;
+  for (int r = 0; r < p.sps; ++r) {
+    const float4 v = p.part[(int64_t)i * p.sps + r];
+    sum += v.x;
+    better(best, bt, v.y, __float_as_int(v.z));
+  }
+  const float floor_ = sum / (float)p.N;
+  p.out[i] = make_float4(floor_ > 0.f ? best / floor_ : 0.f, best, __int_as_float(bt), floor_);
 }
 
 // ---------------------------------------------------------------------------
@@ -394,7 +416,7 @@ cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cud
 }
 
 cudaError_t launch_mix(const MixParams& p, cudaStream_t s) {
-  dim3 grid(p.M / kMixQ, (p.K + kMixKG - 1) / kMixKG, p.nw);
+  dim3 grid(p.M / kMixQ, p.items ? 1 : (p.K + kMixKG - 1) / kMixKG, p.items ? p.n_items : p.nw);
   switch (p.sps) {
     case 1: k_mix<1><<<grid, kMixQ, 0, s>>>(p); break;
     case 2: k_mix<2><<<grid, kMixQ, 0, s>>>(p); break;
@@ -416,6 +438,11 @@ cudaError_t launch_corr(int logM, int loge, const CorrParams& p, cudaStream_t s)
 
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s) {
   k_select<<<1, kSelectThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_stats(const PairStatsParams& p, cudaStream_t s) {
+  k_pair_stats<<<(p.n + 127) / 128, 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@
 
 #include "acq_internal.h"
 #include "atlas_acq.h"
+#include "prop_internal.h"
 
 using atlas::CodeBankParams;
 using atlas::CorrParams;
@@ -78,6 +79,14 @@ struct atlas_acq_ctx {
   int stage_cap = 0;
   int* d_stage_count = nullptr;
   std::string last_error;
+  // proposal-search workspace (grown on first use, kept)
+  int2* d_items = nullptr;
+  int4* d_pairs = nullptr;
+  float4* d_pair_stats = nullptr;
+  int list_cap = 0;
+  atlas_detection* d_fb_out = nullptr;
+  int fb_cap = 0;
+  int* d_fb_count = nullptr;
   // profiling (atlas_acq_profile_begin / _end)
   bool profiling = false;
   std::vector<cudaEvent_t> ev;  // pairs
@@ -99,6 +108,12 @@ int fail_cuda(atlas_acq_ctx* ctx, cudaError_t e) {
   } while (0)
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int __float_as_int_host(float f) {
+  int i;
+  memcpy(&i, &f, sizeof(i));
+  return i;
+}
 int ilog2(int64_t v) {
   int r = 0;
   while ((1ll << r) < v) ++r;
@@ -153,6 +168,11 @@ void free_ctx(atlas_acq_ctx* ctx) {
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_stage_out);
   cudaFree(ctx->d_stage_count);
+  cudaFree(ctx->d_items);
+  cudaFree(ctx->d_pairs);
+  cudaFree(ctx->d_pair_stats);
+  cudaFree(ctx->d_fb_out);
+  cudaFree(ctx->d_fb_count);
   for (auto e : ctx->ev) cudaEventDestroy(e);
   cudaSetDevice(prev);
   delete ctx;
@@ -286,6 +306,103 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   return ATLAS_OK;
 }
 
+// One launch group: windows [w0, w0 + nw) of group g (mix, window transforms,
+// per-code correlation, selection appending to out / d_count).
+int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const float2* x, int64_t S, int W, int w0,
+                 int nw, atlas_cell* cells, atlas_detection* out, int capacity, int* d_count, bool profiling) {
+  const int Cg = (int)g.codes.size();
+  atlas::MixParams m;
+  m.x = x;
+  m.S = S;
+  m.N = g.N;
+  m.M = g.M;
+  m.sps = ctx->sps;
+  m.hop = g.hop;
+  m.w0 = w0;
+  m.nw = nw;
+  m.K = ctx->K;
+  m.inc = ctx->d_inc;
+  m.B = ctx->d_G;
+  CK(atlas::launch_mix(m, st));
+  WindowFftParams a;
+  a.M = g.M;
+  a.sps = ctx->sps;
+  a.K = ctx->K;
+  a.nw = nw;
+  a.tw = g.d_tw;
+  a.G = ctx->d_G;
+  CK(atlas::launch_window_fft(g.logM, g.loge, a, st));
+  if (profiling) ctx->prof_launches += 2;
+  CorrParams b;
+  b.G = ctx->d_G;
+  b.D = g.d_spec;
+  b.tw = g.d_tw;
+  b.tw2 = g.d_tw2;
+  b.part = ctx->d_part;
+  b.S = S;
+  b.N = g.N;
+  b.M = g.M;
+  b.sps = ctx->sps;
+  b.hop = g.hop;
+  b.W = W;
+  b.L = g.L;
+  b.w0 = w0;
+  b.nw = nw;
+  b.K = ctx->K;
+  b.Cg = Cg;
+  b.status = ctx->d_status;
+  const bool timed = profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
+  if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
+  CK(atlas::launch_corr(g.logM, g.loge, b, st));
+  if (timed) {
+    CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st));
+    ctx->ev_used += 1;
+  }
+  if (profiling) {
+    ctx->prof_launches += 1;
+    ctx->prof_corr_launches += 1;
+    ctx->prof_corr_units += (int64_t)nw * Cg * ctx->K;
+  }
+  SelectParams c;
+  c.part = ctx->d_part;
+  c.codes = g.d_codes;
+  c.Cg = Cg;
+  c.C = ctx->C;
+  c.K = ctx->K;
+  c.sps = ctx->sps * g.parts();
+  c.N = g.N;
+  c.W = W;
+  c.w0 = w0;
+  c.nw = nw;
+  c.threshold = ctx->threshold;
+  c.out = out;
+  c.capacity = capacity;
+  c.count = d_count;
+  c.cells = cells;
+  CK(atlas::launch_select(c, st));
+  if (profiling) ctx->prof_launches += 1;
+  return ATLAS_OK;
+}
+
+int launch_refine_all(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, atlas_detection* out,
+                      int capacity, const int* d_count) {
+  if (capacity <= 0) return ATLAS_OK;
+  RefineParams r;
+  r.x = x;
+  r.S = S;
+  r.chips = ctx->d_chips;
+  r.chip_off = ctx->d_chip_off;
+  r.chips_per_code = ctx->d_n_chips;
+  r.hop = ctx->d_hop;
+  r.inc = ctx->d_inc;
+  r.sps = ctx->sps;
+  r.out = out;
+  r.capacity = capacity;
+  r.count = d_count;
+  CK(atlas::launch_refine(r, std::min(capacity, 1024), st));
+  return ATLAS_OK;
+}
+
 // only_group >= 0 restricts the search to one code-length group (autotuning).
 int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, atlas_cell* cells,
              atlas_detection* out, int capacity, int* d_count, int only_group = -1) {
@@ -302,100 +419,17 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
     if (only_group >= 0 && gi != only_group) continue;
     const Group& g = ctx->groups[gi];
     const int W = g.windows(S);
-    const int Cg = (int)g.codes.size();
     int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
     if (g.wc > 0) wc = std::min(wc, g.wc);
     for (int w0 = 0; w0 < W; w0 += wc) {
-      const int nw = std::min(wc, W - w0);
-      atlas::MixParams m;
-      m.x = x;
-      m.S = S;
-      m.N = g.N;
-      m.M = g.M;
-      m.sps = ctx->sps;
-      m.hop = g.hop;
-      m.w0 = w0;
-      m.nw = nw;
-      m.K = ctx->K;
-      m.inc = ctx->d_inc;
-      m.B = ctx->d_G;
-      CK(atlas::launch_mix(m, st));
-      WindowFftParams a;
-      a.M = g.M;
-      a.sps = ctx->sps;
-      a.K = ctx->K;
-      a.nw = nw;
-      a.tw = g.d_tw;
-      a.G = ctx->d_G;
-      CK(atlas::launch_window_fft(g.logM, g.loge, a, st));
-      if (profiling) ctx->prof_launches += 2;
-      CorrParams b;
-      b.G = ctx->d_G;
-      b.D = g.d_spec;
-      b.tw = g.d_tw;
-      b.tw2 = g.d_tw2;
-      b.part = ctx->d_part;
-      b.S = S;
-      b.N = g.N;
-      b.M = g.M;
-      b.sps = ctx->sps;
-      b.hop = g.hop;
-      b.W = W;
-      b.L = g.L;
-      b.w0 = w0;
-      b.nw = nw;
-      b.K = ctx->K;
-      b.Cg = Cg;
-      b.status = ctx->d_status;
-      const bool timed = profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
-      if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
-      CK(atlas::launch_corr(g.logM, g.loge, b, st));
-      if (timed) {
-        CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st));
-        ctx->ev_used += 1;
-      }
-      if (profiling) {
-        ctx->prof_launches += 1;
-        ctx->prof_corr_launches += 1;
-        ctx->prof_corr_units += (int64_t)nw * Cg * ctx->K;
-      }
-      SelectParams c;
-      c.part = ctx->d_part;
-      c.codes = g.d_codes;
-      c.Cg = Cg;
-      c.C = ctx->C;
-      c.K = ctx->K;
-      c.sps = ctx->sps * g.parts();
-      c.N = g.N;
-      c.W = W;
-      c.w0 = w0;
-      c.nw = nw;
-      c.threshold = ctx->threshold;
-      c.out = out;
-      c.capacity = capacity;
-      c.count = d_count;
-      c.cells = cells;
-      CK(atlas::launch_select(c, st));
-      if (profiling) ctx->prof_launches += 1;
+      const int r = launch_chunk(ctx, g, st, x, S, W, w0, std::min(wc, W - w0), cells, out, capacity, d_count,
+                                 profiling);
+      if (r != ATLAS_OK) return r;
     }
   }
-  if (capacity > 0) {
-    RefineParams r;
-    r.x = x;
-    r.S = S;
-    r.chips = ctx->d_chips;
-    r.chip_off = ctx->d_chip_off;
-    r.chips_per_code = ctx->d_n_chips;
-    r.hop = ctx->d_hop;
-    r.inc = ctx->d_inc;
-    r.sps = ctx->sps;
-    r.out = out;
-    r.capacity = capacity;
-    r.count = d_count;
-    CK(atlas::launch_refine(r, std::min(capacity, 1024), st));
-    if (profiling) ctx->prof_launches += 1;
-  }
-  return ATLAS_OK;
+  const int r = launch_refine_all(ctx, st, x, S, out, capacity, d_count);
+  if (r == ATLAS_OK && profiling && capacity > 0) ctx->prof_launches += 1;
+  return r;
 }
 
 int check_run_args(atlas_acq_ctx* ctx, const void* x, int64_t S, const void* out, int capacity,
@@ -651,6 +685,231 @@ int atlas_acq_profile_end(atlas_acq_t ctx, atlas_acq_profile* out) {
   ctx->ev.clear();
   ctx->ev_used = 0;
   ctx->profiling = false;
+  return ATLAS_OK;
+}
+
+int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, const float* d_iq,
+                           int64_t n_samples, int32_t topk, float tau_fb, atlas_detection* d_out, int32_t capacity,
+                           int32_t* d_count, int32_t* h_n_fallback) {
+  const int a = check_run_args(ctx, d_iq, n_samples, d_out, capacity, d_count);
+  if (a != ATLAS_OK) return a;
+  if (!prop || topk < 1 || topk > 32 || !(tau_fb >= 0.f)) return ATLAS_ERR_INVALID_ARG;
+  if (prop->lay.C != ctx->C || prop->lay.K != ctx->K) return ATLAS_ERR_INVALID_ARG;
+  if (ctx->groups.size() != 1 || ctx->groups[0].split || ctx->groups[0].N % 4096) return ATLAS_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Group& g = ctx->groups[0];
+  const int W = g.windows(n_samples);
+  const int K = ctx->K, C = ctx->C, sps = ctx->sps;
+  const float2* x = reinterpret_cast<const float2*>(d_iq);
+  // workspaces
+  if (prop->ws_windows < W) {
+    cudaFree(prop->feat);
+    cudaFree(prop->cand);
+    cudaFree(prop->conf);
+    prop->feat = nullptr;
+    prop->cand = nullptr;
+    prop->conf = nullptr;
+    prop->ws_windows = 0;
+    if (cudaMalloc((void**)&prop->feat, (size_t)W * 4096 * 4) != cudaSuccess ||
+        cudaMalloc((void**)&prop->cand, (size_t)W * 32 * 2 * 4) != cudaSuccess ||
+        cudaMalloc((void**)&prop->conf, (size_t)W * 2 * 4) != cudaSuccess)
+      return ATLAS_ERR_NO_MEMORY;
+    prop->ws_windows = W;
+  }
+  if (ctx->list_cap < W * topk) {
+    cudaFree(ctx->d_items);
+    cudaFree(ctx->d_pairs);
+    cudaFree(ctx->d_pair_stats);
+    ctx->d_items = nullptr;
+    ctx->d_pairs = nullptr;
+    ctx->d_pair_stats = nullptr;
+    ctx->list_cap = 0;
+    if (cudaMalloc((void**)&ctx->d_items, sizeof(int2) * (size_t)W * topk) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_pairs, sizeof(int4) * (size_t)W * topk) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_pair_stats, sizeof(float4) * (size_t)W * topk) != cudaSuccess)
+      return ATLAS_ERR_NO_MEMORY;
+    ctx->list_cap = W * topk;
+  }
+  if (!ctx->d_fb_count && cudaMalloc((void**)&ctx->d_fb_count, sizeof(int)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
+  // 1-2: features and candidates
+  int r = atlas_prop_features(prop, st, d_iq, n_samples, 0, g.hop, g.N, W, prop->feat);
+  if (r != ATLAS_OK) return r;
+  r = atlas_prop_candidates(prop, st, prop->feat, W, topk, prop->cand, prop->conf);
+  if (r != ATLAS_OK) return r;
+  std::vector<int> cand((size_t)W * topk * 2);
+  std::vector<float> conf((size_t)W * 2);
+  CK(cudaMemcpyAsync(cand.data(), prop->cand, cand.size() * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(conf.data(), prop->conf, conf.size() * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // 3: work lists
+  std::vector<int> fallback;
+  std::vector<int2> items;
+  std::vector<int4> pairs;
+  for (int w = 0; w < W; ++w) {
+    if (!(conf[2 * w] >= tau_fb)) {
+      fallback.push_back(w);
+      continue;
+    }
+    std::vector<std::pair<int, int>> seen;  // (bin, item)
+    for (int i = 0; i < topk; ++i) {
+      const int c = cand[((size_t)w * topk + i) * 2], k = cand[((size_t)w * topk + i) * 2 + 1];
+      int item = -1;
+      for (auto& sk : seen)
+        if (sk.first == k) item = sk.second;
+      if (item < 0) {
+        item = (int)items.size();
+        items.push_back(make_int2(w, k));
+        seen.push_back(std::make_pair(k, item));
+      }
+      pairs.push_back(make_int4(item, c, w, k));
+    }
+  }
+  // 4: listed cells, in chunks that fit the window-spectrum workspace
+  std::vector<float4> stats(pairs.size());
+  const int items_per_chunk = std::max<int>(1, (int)(ctx->G_elems / (size_t)g.N));
+  const int pairs_per_chunk = std::max<int>(1, (int)(ctx->part_elems / (size_t)sps));
+  size_t pi = 0;
+  for (int i0 = 0; i0 < (int)items.size();) {
+    // items [i0, i1) and the pairs that use them (pairs are grouped by item order of creation)
+    int i1 = std::min<int>((int)items.size(), i0 + items_per_chunk);
+    size_t p1 = pi;
+    while (p1 < pairs.size() && pairs[p1].x < i1 && (int)(p1 - pi) < pairs_per_chunk) ++p1;
+    if (p1 < pairs.size() && pairs[p1].x < i1) i1 = pairs[p1].x;  // pair budget ran out first
+    if (i1 <= i0) i1 = i0 + 1;
+    std::vector<int2> ci(items.begin() + i0, items.begin() + i1);
+    std::vector<int4> cp;
+    for (size_t q = pi; q < pairs.size() && pairs[q].x < i1; ++q) {
+      int4 v = pairs[q];
+      v.x -= i0;
+      cp.push_back(v);
+    }
+    CK(cudaMemcpyAsync(ctx->d_items, ci.data(), ci.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_pairs, cp.data(), cp.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    atlas::MixParams m;
+    m.x = x;
+    m.S = n_samples;
+    m.N = g.N;
+    m.M = g.M;
+    m.sps = sps;
+    m.hop = g.hop;
+    m.w0 = 0;
+    m.nw = 0;
+    m.K = K;
+    m.inc = ctx->d_inc;
+    m.B = ctx->d_G;
+    m.items = ctx->d_items;
+    m.n_items = (int)ci.size();
+    CK(atlas::launch_mix(m, st));
+    WindowFftParams wf;
+    wf.M = g.M;
+    wf.sps = sps;
+    wf.K = 1;
+    wf.nw = (int)ci.size();
+    wf.tw = g.d_tw;
+    wf.G = ctx->d_G;
+    CK(atlas::launch_window_fft(g.logM, g.loge, wf, st));
+    CorrParams b;
+    b.G = ctx->d_G;
+    b.D = g.d_spec;
+    b.tw = g.d_tw;
+    b.part = ctx->d_part;
+    b.S = n_samples;
+    b.N = g.N;
+    b.M = g.M;
+    b.sps = sps;
+    b.hop = g.hop;
+    b.W = W;
+    b.L = g.L;
+    b.w0 = 0;
+    b.nw = 0;
+    b.K = K;
+    b.Cg = C;
+    b.status = ctx->d_status;
+    b.pairs = ctx->d_pairs;
+    b.n_pairs = (int)cp.size();
+    CK(atlas::launch_corr(g.logM, g.loge, b, st));
+    atlas::PairStatsParams ps;
+    ps.part = ctx->d_part;
+    ps.n = (int)cp.size();
+    ps.sps = sps;
+    ps.N = g.N;
+    ps.out = ctx->d_pair_stats;
+    CK(atlas::launch_pair_stats(ps, st));
+    CK(cudaMemcpyAsync(stats.data() + pi, ctx->d_pair_stats, cp.size() * sizeof(float4), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    pi += cp.size();
+    i0 = i1;
+  }
+  // 5: exhaustive search of the fallback windows (ordered by window, then code)
+  int n_fb = 0;
+  std::vector<atlas_detection> fb;
+  if (!fallback.empty()) {
+    const int cap_fb = (int)fallback.size() * C;
+    if (ctx->fb_cap < cap_fb) {
+      cudaFree(ctx->d_fb_out);
+      ctx->d_fb_out = nullptr;
+      ctx->fb_cap = 0;
+      if (cudaMalloc((void**)&ctx->d_fb_out, sizeof(atlas_detection) * (size_t)cap_fb) != cudaSuccess)
+        return ATLAS_ERR_NO_MEMORY;
+      ctx->fb_cap = cap_fb;
+    }
+    CK(cudaMemsetAsync(ctx->d_fb_count, 0, sizeof(int), st));
+    for (size_t i = 0; i < fallback.size();) {  // runs of consecutive windows share a launch group
+      size_t j = i + 1;
+      const int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)K * g.N))));
+      while (j < fallback.size() && fallback[j] == fallback[j - 1] + 1 && (int)(j - i) < wc) ++j;
+      r = launch_chunk(ctx, g, st, x, n_samples, W, fallback[i], (int)(j - i), nullptr, ctx->d_fb_out, cap_fb,
+                       ctx->d_fb_count, false);
+      if (r != ATLAS_OK) return r;
+      i = j;
+    }
+    CK(cudaMemcpyAsync(&n_fb, ctx->d_fb_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    fb.resize(std::min(n_fb, cap_fb));
+    if (!fb.empty())
+      CK(cudaMemcpy(fb.data(), ctx->d_fb_out, fb.size() * sizeof(atlas_detection), cudaMemcpyDeviceToHost));
+  }
+  // 6: per (window, code) of the listed cells, the best candidate bin (smallest on ties)
+  std::vector<atlas_detection> dets(fb.begin(), fb.end());
+  {
+    std::map<std::pair<int, int>, size_t> best;  // (window, code) -> pair index
+    for (size_t q = 0; q < pairs.size(); ++q) {
+      const auto key = std::make_pair(pairs[q].z, pairs[q].y);
+      auto it = best.find(key);
+      if (it == best.end()) {
+        best[key] = q;
+      } else {
+        const float4 a0 = stats[it->second], a1 = stats[q];
+        if (a1.x > a0.x || (a1.x == a0.x && pairs[q].w < pairs[it->second].w)) it->second = q;
+      }
+    }
+    for (auto& kv : best) {
+      const float4 v = stats[kv.second];
+      if (!(v.x >= ctx->threshold)) continue;
+      atlas_detection d;
+      d.code = kv.first.second;
+      d.window = kv.first.first;
+      d.lag = __float_as_int_host(v.z);
+      d.freq_bin = pairs[kv.second].w;
+      d.score = v.x;
+      d.peak_power = v.y;
+      d.toa = 0.0;
+      dets.push_back(d);
+    }
+  }
+  std::stable_sort(dets.begin(), dets.end(), [](const atlas_detection& u, const atlas_detection& v) {
+    return u.window != v.window ? u.window < v.window : u.code < v.code;
+  });
+  const int n_total = (int)dets.size();
+  const int n_write = std::min(n_total, capacity);
+  if (n_write > 0)
+    CK(cudaMemcpyAsync(d_out, dets.data(), sizeof(atlas_detection) * (size_t)n_write, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_count, &n_total, sizeof(int), cudaMemcpyHostToDevice, st));
+  r = launch_refine_all(ctx, st, x, n_samples, d_out, capacity, d_count);
+  if (r != ATLAS_OK) return r;
+  CK(cudaStreamSynchronize(st));
+  if (h_n_fallback) *h_n_fallback = (int)fallback.size();
   return ATLAS_OK;
 }
 
