@@ -276,3 +276,57 @@ def batch(seed: int = 3, n_streams: int = 8, duration_s=(0.5, 2.0), fs_choices=(
         out.append(Workload(f"batch stream {s}: {S} samples at {fs/1e6:g} MS/s, sps {sps}, {K} bins", x, chips,
                             sps, fs, freqs, 0, tags, sigma))
     return out
+
+
+def proposal_stream(seed: int, n_windows: int, device, n_codes: int = 64, n_chips: int = 8192, sps: int = 8,
+                    fs_hz: float = 8e6, n_bins: int = 63, bin_step_hz: float = 500.0, snr_range=(-25.0, 5.0),
+                    p_empty: float = 0.2, sigma: float = 2048.0, chunk: int = 512):
+    """A device-resident stream laid out as n_windows search windows of
+    N = 2 * chips * sps samples (hop = chips * sps): each hop period holds one
+    transmission with probability 1 - p_empty (code, bin, SNR, phase and an
+    integer start inside the period all uniform; carrier = bin centre plus a
+    jitter of at most a tenth of a step).  Noise from torch's seeded generator
+    on `device`; tag parameters from a seeded numpy generator.  Returns
+    (x [S, 2] float32 tensor, chips, freqs, truth) with truth[w] = (code, bin)
+    or (-1, -1)."""
+    import torch
+    L = n_chips * sps
+    N = 2 * L
+    hop = N - L
+    S = N + (n_windows - 1) * hop
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    x = torch.randn((S, 2), generator=gen, device=device, dtype=torch.float32) * sigma
+    chips = [random_chips(n_chips, seed * 1_000_003 + c) for c in range(n_codes)]
+    chips_t = torch.from_numpy(np.stack(chips).astype(np.float32)).to(device)
+    freqs = (np.arange(n_bins, dtype=np.float64) - (n_bins - 1) / 2) * bin_step_hz
+    rng = np.random.default_rng(seed)
+    truth = []
+    tags = []
+    for w in range(n_windows):
+        if rng.uniform() < p_empty:
+            truth.append((-1, -1))
+            continue
+        c = int(rng.integers(0, n_codes))
+        b = int(rng.integers(0, n_bins))
+        f = float(freqs[b] + rng.uniform(-0.1, 0.1) * bin_step_hz)
+        snr = float(rng.uniform(*snr_range))
+        d = w * hop + int(rng.integers(0, hop))
+        tags.append((d, c, f, tag_amplitude(snr, sigma), float(rng.uniform(0, 2 * math.pi))))
+        truth.append((c, b))
+    t = torch.arange(L, device=device, dtype=torch.int64)
+    xc = torch.view_as_complex(x)
+    for i0 in range(0, len(tags), chunk):
+        part = tags[i0:i0 + chunk]
+        d = torch.tensor([p[0] for p in part], device=device, dtype=torch.int64)
+        code = torch.tensor([p[1] for p in part], device=device, dtype=torch.int64)
+        f = torch.tensor([p[2] for p in part], device=device, dtype=torch.float64)
+        amp = torch.tensor([p[3] for p in part], device=device, dtype=torch.float64)
+        ph0 = torch.tensor([p[4] for p in part], device=device, dtype=torch.float64)
+        idx = d[:, None] + t[None, :]                                       # [n, L]
+        wave = chips_t[code][:, t // sps].to(torch.float64)                 # [n, L]
+        ph = 2 * math.pi * f[:, None] * idx.to(torch.float64) / fs_hz + ph0[:, None]
+        sig = (amp[:, None] * wave * torch.exp(1j * ph)).to(torch.complex64)
+        ok = idx < S
+        xc.index_add_(0, idx[ok], sig[ok])
+    return x, chips, freqs, truth
