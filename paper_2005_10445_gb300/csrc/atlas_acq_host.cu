@@ -741,48 +741,56 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
   CK(cudaMemcpyAsync(cand.data(), prop->cand, cand.size() * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(conf.data(), prop->conf, conf.size() * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  // 3: work lists
+  // 3: work lists, per window: its distinct candidate bins (items) and its
+  // (item, code) cells (pairs); item indices are local to the window
   std::vector<int> fallback;
-  std::vector<int2> items;
-  std::vector<int4> pairs;
+  std::vector<int> win;                       // windows searched over candidates
+  std::vector<std::vector<int2>> win_items;   // (window, bin)
+  std::vector<std::vector<int4>> win_pairs;   // (local item, code, window, bin)
   for (int w = 0; w < W; ++w) {
     if (!(conf[2 * w] >= tau_fb)) {
       fallback.push_back(w);
       continue;
     }
-    std::vector<std::pair<int, int>> seen;  // (bin, item)
+    std::vector<int2> it;
+    std::vector<int4> pr;
     for (int i = 0; i < topk; ++i) {
       const int c = cand[((size_t)w * topk + i) * 2], k = cand[((size_t)w * topk + i) * 2 + 1];
+      if (c < 0 || c >= C || k < 0 || k >= K) return ATLAS_ERR_DEVICE;
       int item = -1;
-      for (auto& sk : seen)
-        if (sk.first == k) item = sk.second;
+      for (int j = 0; j < (int)it.size(); ++j)
+        if (it[j].y == k) item = j;
       if (item < 0) {
-        item = (int)items.size();
-        items.push_back(make_int2(w, k));
-        seen.push_back(std::make_pair(k, item));
+        item = (int)it.size();
+        it.push_back(make_int2(w, k));
       }
-      pairs.push_back(make_int4(item, c, w, k));
+      pr.push_back(make_int4(item, c, w, k));
     }
+    win.push_back(w);
+    win_items.push_back(it);
+    win_pairs.push_back(pr);
   }
-  // 4: listed cells, in chunks that fit the window-spectrum workspace
-  std::vector<float4> stats(pairs.size());
+  // 4: listed cells, in chunks of whole windows that fit the window-spectrum
+  // and partial-result workspaces
+  std::vector<int4> pairs;   // every listed cell, in chunk order (x = global item index)
+  std::vector<float4> stats;
   const int items_per_chunk = std::max<int>(1, (int)(ctx->G_elems / (size_t)g.N));
   const int pairs_per_chunk = std::max<int>(1, (int)(ctx->part_elems / (size_t)sps));
-  size_t pi = 0;
-  for (int i0 = 0; i0 < (int)items.size();) {
-    // items [i0, i1) and the pairs that use them (pairs are grouped by item order of creation)
-    int i1 = std::min<int>((int)items.size(), i0 + items_per_chunk);
-    size_t p1 = pi;
-    while (p1 < pairs.size() && pairs[p1].x < i1 && (int)(p1 - pi) < pairs_per_chunk) ++p1;
-    if (p1 < pairs.size() && pairs[p1].x < i1) i1 = pairs[p1].x;  // pair budget ran out first
-    if (i1 <= i0) i1 = i0 + 1;
-    std::vector<int2> ci(items.begin() + i0, items.begin() + i1);
+  for (size_t v0 = 0; v0 < win.size();) {
+    std::vector<int2> ci;
     std::vector<int4> cp;
-    for (size_t q = pi; q < pairs.size() && pairs[q].x < i1; ++q) {
-      int4 v = pairs[q];
-      v.x -= i0;
-      cp.push_back(v);
+    size_t v1 = v0;
+    while (v1 < win.size() && (v1 == v0 || ((int)(ci.size() + win_items[v1].size()) <= items_per_chunk &&
+                                            (int)(cp.size() + win_pairs[v1].size()) <= pairs_per_chunk))) {
+      const int base = (int)ci.size();
+      for (auto& q : win_pairs[v1]) cp.push_back(make_int4(q.x + base, q.y, q.z, q.w));
+      ci.insert(ci.end(), win_items[v1].begin(), win_items[v1].end());
+      ++v1;
     }
+    if ((int)ci.size() > items_per_chunk || (int)cp.size() > pairs_per_chunk || (int)cp.size() > ctx->list_cap)
+      return ATLAS_ERR_UNSUPPORTED;  // a single window's candidates exceed the workspaces
+    for (auto& q : cp)
+      if (q.x < 0 || q.x >= (int)ci.size()) return ATLAS_ERR_DEVICE;
     CK(cudaMemcpyAsync(ctx->d_items, ci.data(), ci.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->d_pairs, cp.data(), cp.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     atlas::MixParams m;
@@ -835,11 +843,13 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
     ps.N = g.N;
     ps.out = ctx->d_pair_stats;
     CK(atlas::launch_pair_stats(ps, st));
-    CK(cudaMemcpyAsync(stats.data() + pi, ctx->d_pair_stats, cp.size() * sizeof(float4), cudaMemcpyDeviceToHost,
+    const size_t off = stats.size();
+    stats.resize(off + cp.size());
+    CK(cudaMemcpyAsync(stats.data() + off, ctx->d_pair_stats, cp.size() * sizeof(float4), cudaMemcpyDeviceToHost,
                        st));
     CK(cudaStreamSynchronize(st));
-    pi += cp.size();
-    i0 = i1;
+    pairs.insert(pairs.end(), cp.begin(), cp.end());
+    v0 = v1;
   }
   // 5: exhaustive search of the fallback windows (ordered by window, then code)
   int n_fb = 0;

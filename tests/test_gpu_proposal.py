@@ -144,9 +144,9 @@ def test_training_lowers_the_loss(torch_cuda):
     assert float(loss.item()) < 0.5 * first
 
 
-def _proposed(torch, wl, net, topk, tau, cap=256):
+def _proposed(torch, wl, net, topk, tau, cap=256, wpl=0):
     from paper_2005_10445_gb300.binding import DETECTION_DTYPE, Search, run_proposed
-    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len)
+    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len, windows_per_launch=wpl)
     x = torch.from_numpy(wl.iq().copy()).cuda()
     out = torch.zeros(cap * 32, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -167,13 +167,15 @@ def test_proposed_search_full_fallback_equals_exhaustive(torch_cuda):
     assert nfb > 0 and n == n_ref and got.tobytes() == ref.tobytes()
 
 
-def test_proposed_search_covering_candidates_equals_exhaustive(torch_cuda):
+@pytest.mark.parametrize("wpl", [0, 1])
+def test_proposed_search_covering_candidates_equals_exhaustive(torch_cuda, wpl):
     """With top-k covering every (code, bin) pair and no fallback, the listed-cell
-    path reproduces the exhaustive detections bit for bit."""
+    path reproduces the exhaustive detections bit for bit; with one window per
+    launch group the cells are processed in many chunks of whole windows."""
     from paper_2005_10445_gb300.binding import Proposal
     wl = synth.small(seed=12, N=8192)  # 3 codes x 5 bins = 15 pairs
     net = Proposal(len(wl.chips), len(wl.freqs_hz), 2)
-    got, n, ref, n_ref, nfb = _proposed(torch_cuda, wl, net, topk=15, tau=0.0)
+    got, n, ref, n_ref, nfb = _proposed(torch_cuda, wl, net, topk=15, tau=0.0, wpl=wpl)
     assert nfb == 0 and n == n_ref >= 3
     assert got.tobytes() == ref.tobytes()
     ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len)
