@@ -77,7 +77,9 @@ typedef struct {
   int32_t windows_per_launch; /* windows processed per launch group; 0 = automatic */
   int32_t tile_log2;       /* complex values per thread of the transform kernels: 4 -> 16, 5 -> 32;
                               0 = default (32) or the autotuned choice */
-  int32_t reserved[4];
+  int32_t split;           /* 1: run transforms of N/sps = 2^14 as two blocks of 2^13 (always done
+                              for 2^15); 0 = default */
+  int32_t reserved[3];
 } atlas_acq_opts;
 
 /* Fill *opts with the defaults. */
@@ -148,8 +150,9 @@ int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t
                        atlas_detection* h_out, int32_t capacity, int32_t* h_count);
 
 /*
- * Autotune the transform tile shape (16 or 32 complex values per thread) and
- * the windows per launch group of every code-length group of the context, by
+ * Autotune the transform tile shape (16 or 32 complex values per thread), the
+ * split of 2^14-point transforms into two blocks, and the windows per launch
+ * group of every code-length group of the context, by
  * timing each candidate on the caller's stream over the given device samples
  * (Section 4.2 plans FFTs for fixed sizes; this plans our own kernels).  With
  * cache_path (a JSON-lines file, one object per tuned shape keyed by GPU name,
@@ -161,9 +164,10 @@ int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t
 int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t n_samples,
                        const char* cache_path);
 
-/* The tile shape (log2 of values per thread) and windows per launch group in
- * use for the group of code `code`. */
-int atlas_acq_tuning(atlas_acq_t ctx, int32_t code, int32_t* tile_log2, int32_t* windows_per_launch);
+/* The tile shape (log2 of values per thread), windows per launch group and
+ * split flag (two-block transforms) in use for the group of code `code`. */
+int atlas_acq_tuning(atlas_acq_t ctx, int32_t code, int32_t* tile_log2, int32_t* windows_per_launch,
+                     int32_t* split);
 
 /*
  * Batched search over many receiver streams (Section 4.3 batches many

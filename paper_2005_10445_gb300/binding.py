@@ -52,7 +52,7 @@ class Cell(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_float), ("fft_len", ctypes.c_int32),
                 ("windows_per_launch", ctypes.c_int32), ("tile_log2", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Profile(ctypes.Structure):
@@ -111,7 +111,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_acq_run_static.restype = ctypes.c_int
     lib.atlas_acq_autotune.argtypes = [vp, vp, vp, i64, ctypes.c_char_p]
     lib.atlas_acq_autotune.restype = ctypes.c_int
-    lib.atlas_acq_tuning.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.atlas_acq_tuning.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.atlas_acq_tuning.restype = ctypes.c_int
     lib.atlas_acq_batch_create.argtypes = [ctypes.POINTER(vp), vp, i32, vp, vp, vp, i32, vp]
     lib.atlas_acq_batch_create.restype = ctypes.c_int
@@ -175,7 +175,7 @@ class Search:
 
     def __init__(self, chips: Sequence[np.ndarray], samples_per_chip: int, fs_hz: float,
                  freq_offsets_hz: Sequence[float], threshold: float = 25.0, fft_len: int = 0,
-                 windows_per_launch: int = 0, tile_log2: int = 0):
+                 windows_per_launch: int = 0, tile_log2: int = 0, split: int = 0):
         lib = load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -187,6 +187,7 @@ class Search:
         o.fft_len = fft_len
         o.windows_per_launch = windows_per_launch
         o.tile_log2 = tile_log2
+        o.split = split
         self.n_codes = len(chips)
         self.n_freq = len(fr)
         st = lib.atlas_acq_create(ctypes.byref(self.ctx), cat.ctypes.data, cpc.ctypes.data, len(chips),
@@ -242,9 +243,10 @@ class Search:
                                             cache_path.encode() if cache_path else None), self.ctx)
 
     def tuning(self, code: int = 0):
-        t, w = ctypes.c_int32(), ctypes.c_int32()
-        _check(self._lib.atlas_acq_tuning(self.ctx, code, ctypes.byref(t), ctypes.byref(w)))
-        return t.value, w.value
+        """(tile_log2, windows_per_launch, split) of the code's group."""
+        t, w, sp = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.atlas_acq_tuning(self.ctx, code, ctypes.byref(t), ctypes.byref(w), ctypes.byref(sp)))
+        return t.value, w.value, sp.value
 
     def device_status(self) -> int:
         return int(self._lib.atlas_acq_last_device_status(self.ctx))

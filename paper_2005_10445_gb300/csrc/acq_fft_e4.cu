@@ -5,10 +5,12 @@ namespace atlas {
 
 cudaError_t prepare_fft_e4() { return FftLaunch<4>::prepare(); }
 
-cudaError_t launch_window_fft_e4(int logM, const WindowFftParams& p, cudaStream_t s) {
-  return FftLaunch<4>::window_fft(logM, p, s);
+cudaError_t launch_window_fft_e4(int logM, bool split, const WindowFftParams& p, cudaStream_t s) {
+  return FftLaunch<4>::window_fft(logM, split, p, s);
 }
 
-cudaError_t launch_corr_e4(int logM, const CorrParams& p, cudaStream_t s) { return FftLaunch<4>::corr(logM, p, s); }
+cudaError_t launch_corr_e4(int logM, bool split, const CorrParams& p, cudaStream_t s) {
+  return FftLaunch<4>::corr(logM, split, p, s);
+}
 
 }  // namespace atlas

@@ -5,10 +5,12 @@ namespace atlas {
 
 cudaError_t prepare_fft_e5() { return FftLaunch<5>::prepare(); }
 
-cudaError_t launch_window_fft_e5(int logM, const WindowFftParams& p, cudaStream_t s) {
-  return FftLaunch<5>::window_fft(logM, p, s);
+cudaError_t launch_window_fft_e5(int logM, bool split, const WindowFftParams& p, cudaStream_t s) {
+  return FftLaunch<5>::window_fft(logM, split, p, s);
 }
 
-cudaError_t launch_corr_e5(int logM, const CorrParams& p, cudaStream_t s) { return FftLaunch<5>::corr(logM, p, s); }
+cudaError_t launch_corr_e5(int logM, bool split, const CorrParams& p, cudaStream_t s) {
+  return FftLaunch<5>::corr(logM, split, p, s);
+}
 
 }  // namespace atlas

@@ -194,6 +194,16 @@ struct FftLaunch {
                                 (int)fft_smem<LOGM>());
   }
 
+  template <int LOGH>
+  static cudaError_t prepare_split() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_window_fft_split<LOGH, LOGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fft_smem<LOGH>())) != cudaSuccess)
+      return e;
+    return cudaFuncSetAttribute(k_corr_split<LOGH, LOGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fft_smem<LOGH>());
+  }
+
   static cudaError_t prepare() {
     cudaError_t e;
     if ((e = prepare_one<10>()) != cudaSuccess) return e;
@@ -201,45 +211,52 @@ struct FftLaunch {
     if ((e = prepare_one<12>()) != cudaSuccess) return e;
     if ((e = prepare_one<13>()) != cudaSuccess) return e;
     if ((e = prepare_one<14>()) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_window_fft_split<14, LOGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fft_smem<14>())) != cudaSuccess)
-      return e;
-    return cudaFuncSetAttribute(k_corr_split<14, LOGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fft_smem<14>());
+    if ((e = prepare_split<13>()) != cudaSuccess) return e;
+    return prepare_split<14>();
   }
 
-  static cudaError_t window_fft(int logM, const WindowFftParams& p, cudaStream_t s) {
+  // split: the transform of M = 2^logM points as two blocks of 2^(logM-1)
+  // (required for 2^15, optional for 2^14)
+  static cudaError_t window_fft(int logM, bool split, const WindowFftParams& p, cudaStream_t s) {
     dim3 grid(p.sps, p.K, p.nw);
+    dim3 g2(2 * p.sps, p.K, p.nw);
+    if (split) {
+      switch (logM) {
+        case 14: k_window_fft_split<13, LOGE><<<g2, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
+        case 15: k_window_fft_split<14, LOGE><<<g2, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+      }
+      return cudaGetLastError();
+    }
     switch (logM) {
       case 10: k_window_fft<10, LOGE><<<grid, fft_threads<10, LOGE>(), fft_smem<10>(), s>>>(p); break;
       case 11: k_window_fft<11, LOGE><<<grid, fft_threads<11, LOGE>(), fft_smem<11>(), s>>>(p); break;
       case 12: k_window_fft<12, LOGE><<<grid, fft_threads<12, LOGE>(), fft_smem<12>(), s>>>(p); break;
       case 13: k_window_fft<13, LOGE><<<grid, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
       case 14: k_window_fft<14, LOGE><<<grid, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p); break;
-      case 15: {
-        dim3 g2(2 * p.sps, p.K, p.nw);
-        k_window_fft_split<14, LOGE><<<g2, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p);
-        break;
-      }
       default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
   }
 
-  static cudaError_t corr(int logM, const CorrParams& p, cudaStream_t s) {
-    if (p.pairs && logM > 14) return cudaErrorInvalidValue;  // listed cells: single-block sizes only
+  static cudaError_t corr(int logM, bool split, const CorrParams& p, cudaStream_t s) {
+    if (p.pairs && (split || logM > 14)) return cudaErrorInvalidValue;  // listed cells: single-block sizes
     dim3 grid(p.sps, p.pairs ? 1 : p.K, p.pairs ? p.n_pairs : p.nw * p.Cg);
+    dim3 g2(2 * p.sps, p.K, p.nw * p.Cg);
+    if (split) {
+      switch (logM) {
+        case 14: k_corr_split<13, LOGE><<<g2, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
+        case 15: k_corr_split<14, LOGE><<<g2, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+      }
+      return cudaGetLastError();
+    }
     switch (logM) {
       case 10: k_corr<10, LOGE><<<grid, fft_threads<10, LOGE>(), fft_smem<10>(), s>>>(p); break;
       case 11: k_corr<11, LOGE><<<grid, fft_threads<11, LOGE>(), fft_smem<11>(), s>>>(p); break;
       case 12: k_corr<12, LOGE><<<grid, fft_threads<12, LOGE>(), fft_smem<12>(), s>>>(p); break;
       case 13: k_corr<13, LOGE><<<grid, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
       case 14: k_corr<14, LOGE><<<grid, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p); break;
-      case 15: {
-        dim3 g2(2 * p.sps, p.K, p.nw * p.Cg);
-        k_corr_split<14, LOGE><<<g2, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p);
-        break;
-      }
       default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -100,15 +100,17 @@ struct CodeBankParams {
 
 cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cudaStream_t s);
 cudaError_t launch_mix(const MixParams& p, cudaStream_t s);
-// loge: log2 of the complex values per thread of the transform kernels (4 or 5)
-cudaError_t launch_window_fft(int logM, int loge, const WindowFftParams& p, cudaStream_t s);
-cudaError_t launch_corr(int logM, int loge, const CorrParams& p, cudaStream_t s);
+// loge: log2 of the complex values per thread of the transform kernels (4 or 5);
+// split: the transform as two blocks of half the size (required for 2^15,
+// available for 2^14)
+cudaError_t launch_window_fft(int logM, int loge, bool split, const WindowFftParams& p, cudaStream_t s);
+cudaError_t launch_corr(int logM, int loge, bool split, const CorrParams& p, cudaStream_t s);
 cudaError_t prepare_fft_e4();
 cudaError_t prepare_fft_e5();
-cudaError_t launch_window_fft_e4(int logM, const WindowFftParams& p, cudaStream_t s);
-cudaError_t launch_window_fft_e5(int logM, const WindowFftParams& p, cudaStream_t s);
-cudaError_t launch_corr_e4(int logM, const CorrParams& p, cudaStream_t s);
-cudaError_t launch_corr_e5(int logM, const CorrParams& p, cudaStream_t s);
+cudaError_t launch_window_fft_e4(int logM, bool split, const WindowFftParams& p, cudaStream_t s);
+cudaError_t launch_window_fft_e5(int logM, bool split, const WindowFftParams& p, cudaStream_t s);
+cudaError_t launch_corr_e4(int logM, bool split, const CorrParams& p, cudaStream_t s);
+cudaError_t launch_corr_e5(int logM, bool split, const CorrParams& p, cudaStream_t s);
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s);
 cudaError_t launch_pair_stats(const PairStatsParams& p, cudaStream_t s);
 cudaError_t launch_refine(const RefineParams& p, int grid, cudaStream_t s);

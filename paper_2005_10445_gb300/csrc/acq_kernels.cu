@@ -428,12 +428,12 @@ cudaError_t launch_mix(const MixParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_window_fft(int logM, int loge, const WindowFftParams& p, cudaStream_t s) {
-  return loge == 4 ? launch_window_fft_e4(logM, p, s) : launch_window_fft_e5(logM, p, s);
+cudaError_t launch_window_fft(int logM, int loge, bool split, const WindowFftParams& p, cudaStream_t s) {
+  return loge == 4 ? launch_window_fft_e4(logM, split, p, s) : launch_window_fft_e5(logM, split, p, s);
 }
 
-cudaError_t launch_corr(int logM, int loge, const CorrParams& p, cudaStream_t s) {
-  return loge == 4 ? launch_corr_e4(logM, p, s) : launch_corr_e5(logM, p, s);
+cudaError_t launch_corr(int logM, int loge, bool split, const CorrParams& p, cudaStream_t s) {
+  return loge == 4 ? launch_corr_e4(logM, split, p, s) : launch_corr_e5(logM, split, p, s);
 }
 
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s) {

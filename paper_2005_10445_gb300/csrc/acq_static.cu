@@ -204,7 +204,7 @@ extern "C" int atlas_acq_run_static(void* stream, const float* d_iq, int64_t n_s
     a.nw = 1;
     a.tw = tw;
     a.G = G;
-    if (launch_window_fft(logM, 5, a, st) != cudaSuccess) return ATLAS_ERR_CUDA;
+    if (launch_window_fft(logM, 5, false, a, st) != cudaSuccess) return ATLAS_ERR_CUDA;
     CorrParams b;
     b.G = G;
     b.D = D;
@@ -223,7 +223,7 @@ extern "C" int atlas_acq_run_static(void* stream, const float* d_iq, int64_t n_s
     b.K = n_freq;
     b.Cg = 1;
     b.status = nullptr;
-    if (launch_corr(logM, 5, b, st) != cudaSuccess) return ATLAS_ERR_CUDA;
+    if (launch_corr(logM, 5, false, b, st) != cudaSuccess) return ATLAS_ERR_CUDA;
     SelectParams c;
     c.part = part;
     c.codes = &meta->code;

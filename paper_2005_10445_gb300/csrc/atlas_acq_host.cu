@@ -31,14 +31,15 @@ namespace {
 // spectra; each such group is searched by one launch sequence.
 struct Group {
   int n_chips = 0, L = 0, N = 0, M = 0, logM = 0, hop = 0;
-  bool split = false;          // M = 2^15: two-block transforms
+  bool split = false;          // two-block transforms (always for M = 2^15, optional for 2^14)
   int loge = 5;                // log2 of complex values per thread in the transform kernels
   int wc = 0;                  // windows per launch group (0 = the context default)
   std::vector<int> codes;      // global code ids
   int* d_codes = nullptr;      // [Cg]
   float2* d_spec = nullptr;    // [Cg][M] conj(FFT_M(chips)) / M
-  const float2* d_tw = nullptr;   // tables of the block transform (2^14 when split)
-  const float2* d_tw2 = nullptr;  // tables of M (split only)
+  const float2* d_tw_full = nullptr;  // tables of M
+  const float2* d_tw_half = nullptr;  // tables of M / 2
+  const float2* tw() const { return split ? d_tw_half : d_tw_full; }  // tables of the block transform
   int parts() const { return split ? 2 : 1; }  // partial results per (cell, rho)
   int windows(int64_t S) const {
     if (S <= N) return 1;
@@ -217,9 +218,10 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
       g.logM = ilog2(g.M);
       if (g.logM < atlas::kMinLogM || g.logM > atlas::kMaxLogM) return ATLAS_ERR_UNSUPPORTED;
       g.hop = g.N - g.L;
-      g.split = (g.logM == 15);
+      g.split = (g.logM == 15) || (g.logM == 14 && o.split == 1);
       if (o.tile_log2 == 4 || o.tile_log2 == 5) g.loge = o.tile_log2;
       else if (o.tile_log2 != 0) return ATLAS_ERR_INVALID_ARG;
+      if (o.split != 0 && o.split != 1) return ATLAS_ERR_INVALID_ARG;
       by_len[nc] = (int)ctx->groups.size();
       ctx->groups.push_back(g);
       it = by_len.find(nc);
@@ -251,7 +253,7 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   size_t max_part_per_win = 0;
   for (auto& g : ctx->groups) {
     max_win_bytes = std::max(max_win_bytes, (size_t)n_freq * g.N * sizeof(float2));
-    max_part_per_win = std::max(max_part_per_win, (size_t)g.codes.size() * n_freq * sps * g.parts());
+    max_part_per_win = std::max(max_part_per_win, (size_t)g.codes.size() * n_freq * sps * 2);
   }
   int wc = o.windows_per_launch > 0 ? o.windows_per_launch : (int)std::max<size_t>(1, budget / max_win_bytes);
   wc = std::min(wc, 64);
@@ -273,9 +275,9 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
     return ATLAS_OK;
   };
   for (auto& g : ctx->groups) {
-    int st = tables(g.split ? g.logM - 1 : g.logM, &g.d_tw);
+    int st = tables(g.logM, &g.d_tw_full);
     if (st != ATLAS_OK) return st;
-    if (g.split && (st = tables(g.logM, &g.d_tw2)) != ATLAS_OK) return st;
+    if (g.logM > atlas::kMinLogM && (st = tables(g.logM - 1, &g.d_tw_half)) != ATLAS_OK) return st;
     CK(upload(&g.d_codes, g.codes.data(), g.codes.size()));
     if (cudaMalloc((void**)&g.d_spec, sizeof(float2) * (size_t)g.M * g.codes.size()) != cudaSuccess)
       return ATLAS_ERR_NO_MEMORY;
@@ -293,7 +295,7 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
     p.chips = ctx->d_chips;
     p.chip_off = d_goff;
     p.n_chips = d_gn;
-    p.tw = g.d_tw;
+    p.tw = g.logM == 15 ? g.d_tw_half : g.d_tw_full;
     p.D = g.d_spec;
     p.M = g.M;
     p.scale = 1.0f / (float)g.M;
@@ -329,15 +331,15 @@ int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const floa
   a.sps = ctx->sps;
   a.K = ctx->K;
   a.nw = nw;
-  a.tw = g.d_tw;
+  a.tw = g.tw();
   a.G = ctx->d_G;
-  CK(atlas::launch_window_fft(g.logM, g.loge, a, st));
+  CK(atlas::launch_window_fft(g.logM, g.loge, g.split, a, st));
   if (profiling) ctx->prof_launches += 2;
   CorrParams b;
   b.G = ctx->d_G;
   b.D = g.d_spec;
-  b.tw = g.d_tw;
-  b.tw2 = g.d_tw2;
+  b.tw = g.tw();
+  b.tw2 = g.d_tw_full;
   b.part = ctx->d_part;
   b.S = S;
   b.N = g.N;
@@ -353,7 +355,7 @@ int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const floa
   b.status = ctx->d_status;
   const bool timed = profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
   if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
-  CK(atlas::launch_corr(g.logM, g.loge, b, st));
+  CK(atlas::launch_corr(g.logM, g.loge, g.split, b, st));
   if (timed) {
     CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st));
     ctx->ev_used += 1;
@@ -553,19 +555,25 @@ int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t
   cudaStream_t st = (cudaStream_t)stream;
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, ctx->device));
-  // cache: one JSON object per line {"key": "...", "tile_log2": t, "windows_per_launch": w, "ms": m}
-  std::map<std::string, std::pair<int, int>> cache;
+  // cache: one JSON object per line
+  // {"key": "...", "tile_log2": t, "windows_per_launch": w, "split": s, "ms": m}
+  struct Choice {
+    int t, w, s;
+  };
+  std::map<std::string, Choice> cache;
   if (cache_path) {
     std::ifstream in(cache_path);
     std::string line;
     while (std::getline(in, line)) {
       char key[512];
-      int t = 0, w = 0;
+      int t = 0, w = 0, sp = 0;
       double ms = 0.0;
-      if (sscanf(line.c_str(), "{\"key\": \"%511[^\"]\", \"tile_log2\": %d, \"windows_per_launch\": %d, \"ms\": %lf}",
-                 key, &t, &w, &ms) == 4 &&
-          (t == 4 || t == 5) && w >= 1)
-        cache[key] = std::make_pair(t, w);
+      if (sscanf(line.c_str(),
+                 "{\"key\": \"%511[^\"]\", \"tile_log2\": %d, \"windows_per_launch\": %d, \"split\": %d, "
+                 "\"ms\": %lf}",
+                 key, &t, &w, &sp, &ms) == 5 &&
+          (t == 4 || t == 5) && w >= 1 && (sp == 0 || sp == 1))
+        cache[key] = Choice{t, w, sp};
     }
   }
   atlas_detection* d_out = nullptr;
@@ -593,8 +601,9 @@ int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t
     const std::string key = ks.str();
     auto it = cache.find(key);
     if (it != cache.end()) {
-      g.loge = it->second.first;
-      g.wc = it->second.second;
+      g.loge = it->second.t;
+      g.wc = it->second.w;
+      g.split = g.logM == 15 || (g.logM == 14 && it->second.s == 1);
       continue;
     }
     // time on (at most) the first 32 windows of the group
@@ -602,12 +611,19 @@ int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t
     const int W = g.windows(S_tune);
     const int fit = std::max(1, (int)(ctx->G_elems / ((size_t)ctx->K * g.N)));
     int best_t = g.loge, best_w = g.wc;
+    bool best_s = g.split;
     double best_ms = 1e30;
+    std::vector<bool> splits;
+    if (g.logM == 15) splits = {true};
+    else if (g.logM == 14) splits = {false, true};
+    else splits = {false};
+    for (bool sp : splits)
     for (int t : {5, 4}) {
       for (int w : {1, 2, 4, 8}) {
         if (w > std::min(fit, ctx->wc_max) || (w > 1 && w >= 2 * W)) continue;
         g.loge = t;
         g.wc = w;
+        g.split = sp;
         int r = run_impl(ctx, st, reinterpret_cast<const float2*>(d_iq), S_tune, nullptr, d_out, 64, d_count, gi);
         if (r != ATLAS_OK) {
           status = r;
@@ -627,15 +643,17 @@ int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t
           best_ms = ms / 2;
           best_t = t;
           best_w = w;
+          best_s = sp;
         }
       }
       if (status != ATLAS_OK) break;
     }
     g.loge = best_t;
     g.wc = best_w;
+    g.split = best_s;
     if (status == ATLAS_OK && outf.is_open())
       outf << "{\"key\": \"" << key << "\", \"tile_log2\": " << best_t << ", \"windows_per_launch\": " << best_w
-           << ", \"ms\": " << best_ms << "}\n";
+           << ", \"split\": " << (best_s ? 1 : 0) << ", \"ms\": " << best_ms << "}\n";
   }
   ctx->profiling = was_profiling;
   cudaFree(d_out);
@@ -645,10 +663,12 @@ int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t
   return status;
 }
 
-int atlas_acq_tuning(atlas_acq_t ctx, int32_t code, int32_t* tile_log2, int32_t* windows_per_launch) {
+int atlas_acq_tuning(atlas_acq_t ctx, int32_t code, int32_t* tile_log2, int32_t* windows_per_launch,
+                     int32_t* split) {
   if (!ctx || code < 0 || code >= ctx->C) return ATLAS_ERR_INVALID_ARG;
   const Group& g = ctx->groups[ctx->code_group[code]];
   if (tile_log2) *tile_log2 = g.loge;
+  if (split) *split = g.split ? 1 : 0;
   if (windows_per_launch) {
     const int fit = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
     *windows_per_launch = g.wc > 0 ? std::min(g.wc, fit) : fit;
@@ -695,7 +715,7 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
   if (a != ATLAS_OK) return a;
   if (!prop || topk < 1 || topk > 32 || !(tau_fb >= 0.f)) return ATLAS_ERR_INVALID_ARG;
   if (prop->lay.C != ctx->C || prop->lay.K != ctx->K) return ATLAS_ERR_INVALID_ARG;
-  if (ctx->groups.size() != 1 || ctx->groups[0].split || ctx->groups[0].N % 4096) return ATLAS_ERR_UNSUPPORTED;
+  if (ctx->groups.size() != 1 || ctx->groups[0].logM > 14 || ctx->groups[0].N % 4096) return ATLAS_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   const Group& g = ctx->groups[0];
   const int W = g.windows(n_samples);
@@ -813,13 +833,13 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
     wf.sps = sps;
     wf.K = 1;
     wf.nw = (int)ci.size();
-    wf.tw = g.d_tw;
+    wf.tw = g.d_tw_full;
     wf.G = ctx->d_G;
-    CK(atlas::launch_window_fft(g.logM, g.loge, wf, st));
+    CK(atlas::launch_window_fft(g.logM, g.loge, false, wf, st));
     CorrParams b;
     b.G = ctx->d_G;
     b.D = g.d_spec;
-    b.tw = g.d_tw;
+    b.tw = g.d_tw_full;
     b.part = ctx->d_part;
     b.S = n_samples;
     b.N = g.N;
@@ -835,7 +855,7 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
     b.status = ctx->d_status;
     b.pairs = ctx->d_pairs;
     b.n_pairs = (int)cp.size();
-    CK(atlas::launch_corr(g.logM, g.loge, b, st));
+    CK(atlas::launch_corr(g.logM, g.loge, false, b, st));
     atlas::PairStatsParams ps;
     ps.part = ctx->d_part;
     ps.n = (int)cp.size();

@@ -110,16 +110,18 @@ def test_small_parity_all_cells(torch_cuda, seed):
     (9000, 4, 131072),   # M = 2^15, sps 4
 ])
 def test_sizes_parity(torch_cuda, n_chips, sps, N):
-    """Every transform size and both tile shapes (16 and 32 values per thread)
-    against the oracle, cell by cell."""
+    """Every transform size, both tile shapes (16 and 32 values per thread) and,
+    for 2^14 points, both the one-block and the two-block transforms, against
+    the oracle cell by cell."""
     L = n_chips * sps
     S = 2 * N + 3 * (N - L) // 2 + 17   # ragged last window
     wl = synth.realistic(seed=n_chips + sps, seconds=S / 4e6, n_codes=2, n_chips=n_chips, sps=sps,
                          fs_hz=4e6, n_tags=2, snr_range=(-8.0, -2.0),
                          freqs_hz=np.array([-2500.0, 0.0, 2500.0]), min_same_code_gap=2 * N, fft_len=N)
     ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len)
-    for tile in (5, 4):
-        s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True, tile_log2=tile)
+    shapes = [(5, 0), (4, 0)] + ([(5, 1), (4, 1)] if N // sps == 1 << 14 else [])
+    for tile, split in shapes:
+        s, dets, n, cells = gpu_search(torch_cuda, wl, cells=True, tile_log2=tile, split=split)
         assert n == len(ora)
         compare_detections(dets, ora)
         W = cells.shape[0]
