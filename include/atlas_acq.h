@@ -79,7 +79,12 @@ typedef struct {
                               0 = default (32) or the autotuned choice */
   int32_t split;           /* 1: run transforms of N/sps = 2^14 as two blocks of 2^13 (always done
                               for 2^15); 0 = default */
-  int32_t reserved[3];
+  int32_t precision;       /* 0: FP32 (default); 1 / 2: the per-code inverse transforms of codes with
+                              N/sps = 2^14 as radix-16 tensor-core contractions with FP16 / BF16
+                              operands, FP32 accumulation and per-stage power-of-two scaling
+                              (other sizes stay FP32); window transforms and the refinement are
+                              unchanged */
+  int32_t reserved[2];
 } atlas_acq_opts;
 
 /* Fill *opts with the defaults. */

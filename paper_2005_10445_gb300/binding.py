@@ -52,7 +52,7 @@ class Cell(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_float), ("fft_len", ctypes.c_int32),
                 ("windows_per_launch", ctypes.c_int32), ("tile_log2", ctypes.c_int32),
-                ("split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("split", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Profile(ctypes.Structure):
@@ -175,7 +175,7 @@ class Search:
 
     def __init__(self, chips: Sequence[np.ndarray], samples_per_chip: int, fs_hz: float,
                  freq_offsets_hz: Sequence[float], threshold: float = 25.0, fft_len: int = 0,
-                 windows_per_launch: int = 0, tile_log2: int = 0, split: int = 0):
+                 windows_per_launch: int = 0, tile_log2: int = 0, split: int = 0, precision: int = 0):
         lib = load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -188,6 +188,7 @@ class Search:
         o.windows_per_launch = windows_per_launch
         o.tile_log2 = tile_log2
         o.split = split
+        o.precision = precision
         self.n_codes = len(chips)
         self.n_freq = len(fr)
         st = lib.atlas_acq_create(ctypes.byref(self.ctx), cat.ctypes.data, cpc.ctypes.data, len(chips),

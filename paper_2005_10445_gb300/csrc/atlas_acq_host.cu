@@ -56,6 +56,7 @@ struct atlas_acq_ctx {
   float threshold = 25.f;
   int max_L = 0;
   int windows_per_launch = 0;
+  int precision = 0;  // 0 FP32; 1 / 2: FP16 / BF16 tensor-core inverse transforms (M = 2^14)
   std::vector<int> n_chips;
   std::vector<double> freqs;
   std::vector<Group> groups;
@@ -195,6 +196,7 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   ctx->fs = fs_hz;
   ctx->threshold = o.threshold;
   ctx->windows_per_launch = o.windows_per_launch;
+  ctx->precision = o.precision;
   ctx->freqs.assign(freqs, freqs + n_freq);
   ctx->n_chips.assign(chips_per_code, chips_per_code + n_codes);
 
@@ -355,7 +357,8 @@ int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const floa
   b.status = ctx->d_status;
   const bool timed = profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
   if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
-  CK(atlas::launch_corr(g.logM, g.loge, g.split, b, st));
+  if (ctx->precision != 0 && g.logM == 14 && !g.split) CK(atlas::launch_corr_tc(ctx->precision, b, st));
+  else CK(atlas::launch_corr(g.logM, g.loge, g.split, b, st));
   if (timed) {
     CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st));
     ctx->ev_used += 1;
@@ -470,7 +473,8 @@ int atlas_acq_create(atlas_acq_t* out, const int8_t* chips, const int32_t* chips
   atlas_acq_opts o;
   atlas_acq_default_opts(&o);
   if (opts) o = *opts;
-  if (!(o.threshold >= 0.f) || o.fft_len < 0 || o.windows_per_launch < 0) return ATLAS_ERR_INVALID_ARG;
+  if (!(o.threshold >= 0.f) || o.fft_len < 0 || o.windows_per_launch < 0 || o.precision < 0 || o.precision > 2)
+    return ATLAS_ERR_INVALID_ARG;
   atlas_acq_ctx* ctx = new (std::nothrow) atlas_acq_ctx();
   if (!ctx) return ATLAS_ERR_NO_MEMORY;
   const int st = create_impl(ctx, chips, chips_per_code, n_codes, samples_per_chip, fs_hz, freq_offsets_hz,
