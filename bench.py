@@ -319,6 +319,73 @@ def run_learned(args, rank: int, world: int, dev, torch, dist) -> None:
         print(json.dumps(line), flush=True)
 
 
+def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
+    """Reduced-precision row: the realistic workload with the per-code inverse
+    transforms in FP32 (CUDA cores) and as FP16 / BF16 tensor-core contractions;
+    throughput, speedup over FP32, agreement of the detections with FP32, and
+    score / ToA error against the FP64 oracle on the injected tags' cells."""
+    from oracle import acq
+    from paper_2005_10445_gb300 import binding
+    wl = make_workload(2 + rank)
+    S = wl.n_samples
+    x = torch.from_numpy(wl.iq().copy()).to(dev)
+    cap = args.capacity
+    out = torch.empty(cap * 32, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    res, dets = {}, {}
+    for prec in (0, 1, 2):
+        srch = binding.Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len, precision=prec)
+        for _ in range(args.warmup):
+            srch.run_ptr(st.cuda_stream, x.data_ptr(), S, out.data_ptr(), cap, cnt.data_ptr())
+        srch.profile_begin(65536)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize(dev)
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(st)
+            srch.run_ptr(st.cuda_stream, x.data_ptr(), S, out.data_ptr(), cap, cnt.data_ptr())
+            evs[i][1].record(st)
+        torch.cuda.synchronize(dev)
+        pr = srch.profile_end()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        n = int(cnt.item())
+        d = out.cpu().numpy().view(binding.DETECTION_DTYPE)[: min(n, cap)].copy()
+        dets[prec] = d
+        res[prec] = {"ms_per_step": ms, "value": S / (ms / 1e3) / 1e6,
+                     "k_corr_ms_per_launch": pr["corr_ms"] / max(pr["timed_launches"], 1), "detections": n}
+        srch.close()
+    key = lambda d: (int(d["code"]), int(d["window"]), int(d["lag"]), int(d["freq_bin"]))
+    ref = {key(d): d for d in dets[0]}
+    W, hop = acq.window_plan(S, wl.fft_len, len(wl.chips[0]) * wl.sps)
+    pairs = sorted({(min(int(t.delay) // hop, W - 1), t.code) for t in wl.tags})
+    ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len, pairs=pairs)
+    ob = {o.key(): o for o in ora}
+    for prec in (0, 1, 2):
+        got = {key(d): d for d in dets[prec]}
+        score_err = [abs(float(got[k]["score"]) / ob[k].score - 1) for k in ob if k in got]
+        toa_err = [abs(float(got[k]["toa"]) - ob[k].toa) for k in ob if k in got]
+        res[prec].update({
+            "speedup_vs_fp32": res[0]["ms_per_step"] / res[prec]["ms_per_step"],
+            "fp32_detections_reproduced": len(set(got) & set(ref)) / max(len(ref), 1),
+            "extra_vs_fp32": len(set(got) - set(ref)),
+            "oracle_tag_cells_found": sum(k in got for k in ob) / max(len(ob), 1),
+            "max_score_rel_err_vs_oracle": max(score_err or [0.0]),
+            "max_toa_err_vs_oracle": max(toa_err or [0.0])})
+    if rank == 0:
+        names = {0: "fp32", 1: "fp16-tc", 2: "bf16-tc"}
+        line = {"metric": METRIC, "value": res[1]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res[1]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f16 tensor-core contractions, f32 accumulate",
+                "data": "synthetic",
+                "config": {"workload": "precision: " + WORKLOAD,
+                           "l2": "flushed before each step (256 MiB write), outside the timed events",
+                           "oracle_cells": f"{len(pairs)} (window, code) pairs of the injected tags, all bins"},
+                "per_precision": {names[p]: r for p, r in res.items()}}
+        print(json.dumps(line), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,7 +394,7 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--capacity", type=int, default=4096)
-    ap.add_argument("--workload", default="realistic", choices=["realistic", "batching", "learned"])
+    ap.add_argument("--workload", default="realistic", choices=["realistic", "batching", "learned", "precision"])
     ap.add_argument("--train-windows", type=int, default=20000)
     ap.add_argument("--test-windows", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=6)
@@ -355,8 +422,9 @@ def main() -> None:
         dist.init_process_group("nccl", device_id=dev)
     if not os.path.exists(binding.LIB_PATH):
         build()
-    if args.workload in ("batching", "learned"):
-        (run_batching if args.workload == "batching" else run_learned)(args, rank, world, dev, torch, dist)
+    if args.workload in ("batching", "learned", "precision"):
+        {"batching": run_batching, "learned": run_learned, "precision": run_precision}[args.workload](
+            args, rank, world, dev, torch, dist)
         if world > 1:
             dist.destroy_process_group()
         return
