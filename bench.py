@@ -276,7 +276,7 @@ def run_learned(args, rank: int, world: int, dev, torch, dist) -> None:
     n_train, n_test = args.train_windows, args.test_windows
     cap = max(1 << 16, 4 * n_train)
     t0 = time.perf_counter()
-    x_tr, chips, freqs, _ = synth.proposal_stream(5 + 100 * rank, n_train, dev)
+    x_tr, chips, freqs, _ = synth.proposal_stream(5 + 100 * rank, n_train, dev, code_seed=5)
     S_tr = x_tr.shape[0]
     # T = 50: at up to +5 dB over 64 codes, a strong tag's real-valued cross-correlation
     # with the other codes peaks at 25-30 times its floor, so T = 25 would label sidelobes
@@ -289,7 +289,7 @@ def run_learned(args, rank: int, world: int, dev, torch, dist) -> None:
     hist = learned.train(prop, feat, code, bin_, torch, epochs=args.epochs)
     del x_tr, feat
     torch.cuda.empty_cache()
-    x_te, _, _, truth = synth.proposal_stream(6 + 100 * rank, n_test, dev)
+    x_te, _, _, truth = synth.proposal_stream(6 + 100 * rank, n_test, dev, code_seed=5)
     S_te = x_te.shape[0]
     learned.exhaustive(search, x_te, S_te, cap, torch)  # warm
     exh, n_exh, t_exh = learned.exhaustive(search, x_te, S_te, cap, torch)

@@ -254,9 +254,10 @@ int atlas_prop_candidates(atlas_prop_t p, void* stream, const float* d_feat, int
 
 /*
  * Search with the proposal: features and candidates for every window of the
- * context's single code length; each window whose top-pair probability is at
- * least tau_fb is searched only over its top-k (code, bin) candidates (per code,
- * the best of its candidate bins), every other window by the exhaustive search.
+ * context's single code length; each window where the network is confident --
+ * max(probability of its top pair, 1 - presence probability) >= tau_fb -- is
+ * searched only over its top-k (code, bin) candidates (per code, the best of
+ * its candidate bins), every other window by the exhaustive search.
  * Output as atlas_acq_run (ordered by window, then code; refined ToA).
  * h_n_fallback (host, may be NULL) receives the number of exhaustive windows.
  * Synchronous: it reads the candidates on the host to build the work lists, and

@@ -39,6 +39,16 @@ constexpr int kSmemElems = kM + 2 * (kM / 1024);
 
 __device__ __forceinline__ int tpad(int i) { return i + 2 * (i >> 10); }
 
+// cos and sin of 2 pi m / 16, m = 0 .. 15 (the 16-point DFT matrix entries)
+__constant__ float kCos16[16] = {1.000000000f,  0.923879533f,  0.707106781f,  0.382683432f,
+                                 0.000000000f,  -0.382683432f, -0.707106781f, -0.923879533f,
+                                 -1.000000000f, -0.923879533f, -0.707106781f, -0.382683432f,
+                                 0.000000000f,  0.382683432f,  0.707106781f,  0.923879533f};
+__constant__ float kSin16[16] = {0.000000000f,  0.382683432f,  0.707106781f,  0.923879533f,
+                                 1.000000000f,  0.923879533f,  0.707106781f,  0.382683432f,
+                                 0.000000000f,  -0.382683432f, -0.707106781f, -0.923879533f,
+                                 -1.000000000f, -0.923879533f, -0.707106781f, -0.382683432f};
+
 template <int PREC>
 struct Op;
 template <>
@@ -153,8 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_corr_tc(CorrParams p) {
       for (int q = 0; q < 4; ++q) {
         const int a = 2 * t4 + (q & 1) + ((q >> 1) << 3);  // row within the k-step
         const int b = (8 * nt + g) & 15;                   // column within the quadrant
-        float s, co;
-        sincospif((float)((a * b) & 15) * 0.125f, &s, &co);
+        const float s = kSin16[(a * b) & 15], co = kCos16[(a * b) & 15];
         const bool im_out = nt >= 2;
         v[q] = ks == 0 ? (im_out ? s : co) : (im_out ? co : -s);
       }
@@ -228,10 +237,15 @@ __global__ void __launch_bounds__(kThreads) k_corr_tc(CorrParams p) {
         for (int g2 = 0; g2 < 2; ++g2) {
           const int j = 64 * warp + 16 * mt + g + 8 * g2;
           const int jm = j & (Ns2 - 1);
+          // W^{jm r} for r = 2t, 2t+1, 2t+8, 2t+9: two table values, two products by W^{jm}
+          const float2 w1 = twiddle<kLogM, +1>(sm_tw, jm << sh);
+          const float2 wa = twiddle<kLogM, +1>(sm_tw, (jm * 2 * t4) << sh);
+          const float2 wb = twiddle<kLogM, +1>(sm_tw, (jm * (2 * t4 + 8)) << sh);
+          const float2 tw4[4] = {wa, cmul(wa, w1), wb, cmul(wb, w1)};
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
             const int r = 2 * t4 + (cc & 1) + ((cc >> 1) << 3);
-            const float2 v = cmul(sm[tpad(j + 1024 * r)], twiddle<kLogM, +1>(sm_tw, (jm * r) << sh));
+            const float2 v = cmul(sm[tpad(j + 1024 * r)], tw4[cc]);
             x[mt][g2][cc] = v;
             mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
           }

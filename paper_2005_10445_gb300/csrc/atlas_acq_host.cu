@@ -772,7 +772,8 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
   std::vector<std::vector<int2>> win_items;   // (window, bin)
   std::vector<std::vector<int4>> win_pairs;   // (local item, code, window, bin)
   for (int w = 0; w < W; ++w) {
-    if (!(conf[2 * w] >= tau_fb)) {
+    // confident: sure of a (code, bin) pair, or sure the window holds no transmission
+    if (!(std::max(conf[2 * w], 1.f - conf[2 * w + 1]) >= tau_fb)) {
       fallback.push_back(w);
       continue;
     }

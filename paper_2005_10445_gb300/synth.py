@@ -280,13 +280,14 @@ def batch(seed: int = 3, n_streams: int = 8, duration_s=(0.5, 2.0), fs_choices=(
 
 def proposal_stream(seed: int, n_windows: int, device, n_codes: int = 64, n_chips: int = 8192, sps: int = 8,
                     fs_hz: float = 8e6, n_bins: int = 63, bin_step_hz: float = 500.0, snr_range=(-25.0, 5.0),
-                    p_empty: float = 0.2, sigma: float = 2048.0, chunk: int = 512):
+                    p_empty: float = 0.2, sigma: float = 2048.0, chunk: int = 512, code_seed: Optional[int] = None):
     """A device-resident stream laid out as n_windows search windows of
     N = 2 * chips * sps samples (hop = chips * sps): each hop period holds one
     transmission with probability 1 - p_empty (code, bin, SNR, phase and an
     integer start inside the period all uniform; carrier = bin centre plus a
     jitter of at most a tenth of a step).  Noise from torch's seeded generator
-    on `device`; tag parameters from a seeded numpy generator.  Returns
+    on `device`; tag parameters from a seeded numpy generator; the codes from
+    code_seed (default: seed), so training and test streams can share a bank.  Returns
     (x [S, 2] float32 tensor, chips, freqs, truth) with truth[w] = (code, bin)
     or (-1, -1)."""
     import torch
@@ -297,7 +298,8 @@ def proposal_stream(seed: int, n_windows: int, device, n_codes: int = 64, n_chip
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     x = torch.randn((S, 2), generator=gen, device=device, dtype=torch.float32) * sigma
-    chips = [random_chips(n_chips, seed * 1_000_003 + c) for c in range(n_codes)]
+    cs = seed if code_seed is None else code_seed
+    chips = [random_chips(n_chips, cs * 1_000_003 + c) for c in range(n_codes)]
     chips_t = torch.from_numpy(np.stack(chips).astype(np.float32)).to(device)
     freqs = (np.arange(n_bins, dtype=np.float64) - (n_bins - 1) / 2) * bin_step_hz
     rng = np.random.default_rng(seed)
