@@ -52,7 +52,7 @@ def flops_per_cell(N: int) -> float:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("acq_kernels.cu", "fft_block.cuh"):
+    for f in ("acq_fft_kernels.cuh", "acq_common.cuh", "fft_block.cuh"):
         with open(os.path.join(ROOT, "paper_2005_10445_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -60,7 +60,7 @@ def kernel_source_hash() -> str:
 
 def ncu_traffic():
     """DRAM bytes per launch of the correlation kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel source and launch size."""
     p = os.path.join(ROOT, "profiles", "k_corr_realistic_traffic.txt")
     if not os.path.exists(p):
         return None

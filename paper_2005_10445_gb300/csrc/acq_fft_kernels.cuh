@@ -98,10 +98,14 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
   const int qlim = (nvalid - rho + sps - 1) / sps;
   float sum = 0.f, best = -1.f;
   int bq = 0x7fffffff;
+  // a thread's outputs arrive in increasing q: the first maximum is the smallest lag
   auto emit = [&](int q, float2 v) {
     const float P = fmaf(v.x, v.x, v.y * v.y);
     sum += P;
-    if (q < qlim) better(best, bq, P, q);
+    if (q < qlim && P > best) {
+      best = P;
+      bq = q;
+    }
   };
   FFT::run(sm, sm_tw, load, emit);
   int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
@@ -163,11 +167,14 @@ __global__ void __launch_bounds__(fft_threads<LOGH, LOGE>()) k_corr_split(CorrPa
   const int qlim = (nvalid - rho + sps - 1) / sps;
   float sum = 0.f, best = -1.f;
   int bq = 0x7fffffff;
-  auto emit = [&](int kk, float2 v) {
+  auto emit = [&](int kk, float2 v) {  // increasing kk, so increasing q
     const int q = 2 * kk + h;
     const float P = fmaf(v.x, v.x, v.y * v.y);
     sum += P;
-    if (q < qlim) better(best, bq, P, q);
+    if (q < qlim && P > best) {
+      best = P;
+      bq = q;
+    }
   };
   FFT::run(sm, sm_tw, load, emit);
   int bt = bq == 0x7fffffff ? bq : bq * sps + rho;

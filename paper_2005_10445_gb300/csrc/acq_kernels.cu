@@ -27,8 +27,9 @@
 //                 the correlation never leaves the chip
 //   k_select      per (w, c): combine the sps partial results of each bin,
 //                 score = P_max / floor, best bin, threshold, ordered compaction
-//   k_refine      per detection: FP64 direct |corr|^2 at a-1, a, a+1 and the
-//                 parabola vertex (Section 3 step 8, "interpolated")
+//   k_refine      per detection: direct |corr|^2 at a-1, a, a+1 (exact fixed-point
+//                 phase, FP32 rotation, FP64 accumulation) and the parabola
+//                 vertex in FP64 (Section 3 step 8, "interpolated")
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -300,42 +301,22 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams p) {
     const int8_t* ch = p.chips + p.chip_off[c];
     const int64_t a = (int64_t)det.window * p.hop[c] + det.lag;
     const uint64_t inc = p.inc[det.freq_bin];
-    // m runs over [a-1, a+L]; thread t takes m = a - 1 + t + kRefineThreads*i.
-    const int64_t m0 = a - 1 + threadIdx.x;
-    const uint64_t step_ph = inc * (uint64_t)kRefineThreads;
-    double sr, cr;
-    sincospi(2.0 * (double)(int64_t)step_ph * 5.42101086242752217e-20, &sr, &cr);  // 2^-64
-    const double str = cr, sti = -sr;  // exp(-2 pi i f * 256 / fs)
-    double s0, c0;
-    sincospi(2.0 * (double)(int64_t)(inc * (uint64_t)m0) * 5.42101086242752217e-20, &s0, &c0);
-    double er = c0, ei = -s0;  // exp(-2 pi i f m / fs)
-    double acc[6] = {0, 0, 0, 0, 0, 0};  // re/im for d = -1, 0, +1
-    int it = 0;
-    for (int64_t m = m0; m <= a + L; m += kRefineThreads, ++it) {
-      if ((it & 15) == 15) {  // re-anchor the rotation every 16 steps
-        sincospi(2.0 * (double)(int64_t)(inc * (uint64_t)m) * 5.42101086242752217e-20, &s0, &c0);
-        er = c0;
-        ei = -s0;
-      }
-      double xr = 0.0, xi = 0.0;
-      if (m >= 0 && m < p.S) {
-        const float2 xv = p.x[m];
-        xr = xv.x;
-        xi = xv.y;
-      }
-      const double yr = xr * er - xi * ei, yi = xr * ei + xi * er;
+    // y[m] = x[m] exp(-2 pi i f m / fs) for m in [a-1, a+L]: the phase is the exact
+    // 64-bit fixed-point product m * inc, the rotation FP32; the three direct
+    // correlations sum_n y[a+d+n] r[n] (d = -1, 0, +1) accumulate in FP64.
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t m = a - 1 + threadIdx.x; m <= a + L; m += kRefineThreads) {
+      if (m < 0 || m >= p.S) continue;
+      const float2 y = cmul(p.x[m], expi_neg(inc * (uint64_t)m));
 #pragma unroll
       for (int d = -1; d <= 1; ++d) {
         const int64_t nn = m - a - d;
         if (nn >= 0 && nn < L) {
-          const double rv = (double)ch[nn / sps];
-          acc[2 * (d + 1)] += yr * rv;
-          acc[2 * (d + 1) + 1] += yi * rv;
+          const bool neg = ch[nn / sps] < 0;
+          acc[2 * (d + 1)] += neg ? -(double)y.x : (double)y.x;
+          acc[2 * (d + 1) + 1] += neg ? -(double)y.y : (double)y.y;
         }
       }
-      const double nr = er * str - ei * sti, ni = er * sti + ei * str;
-      er = nr;
-      ei = ni;
     }
 #pragma unroll
     for (int j = 0; j < 6; ++j) dadd_shfl(acc[j]);

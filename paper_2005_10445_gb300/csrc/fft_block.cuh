@@ -209,8 +209,7 @@ struct BlockFFT {
       dft_reg<R, DIR>(v + s * R);
       const int ob = ((j >> D) << (D + RB)) + (j & ((1 << D) - 1));
       if constexpr (LAST) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) emit(ob + (r << D), v[s * R + r]);
+        // emitted below, in increasing output index
       } else if constexpr (OUT_CLOSED) {
         float2* dst = sm + spad(ob);
 #pragma unroll
@@ -220,7 +219,16 @@ struct BlockFFT {
         for (int r = 0; r < R; ++r) sm[spad(ob + (r << D))] = v[s * R + r];
       }
     }
-    if constexpr (!LAST) __syncthreads();
+    if constexpr (LAST) {
+      // the last pass's outputs of this thread are j_s + r * 2^D with
+      // j_s = t + T s < 2^D: emitting r-major, s-minor gives increasing indices
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int s = 0; s < S; ++s) emit(t + T * s + (r << D), v[s * R + r]);
+    } else {
+      __syncthreads();
+    }
   }
 
   template <int D, class Load, class Emit, class Hook>
@@ -235,7 +243,8 @@ struct BlockFFT {
 
   // Full transform: x[i] = load(i) for i < M; emit(k, X[k]) for k < M, unnormalised,
   // X[k] = sum_i x[i] exp(DIR * 2 pi i * i k / M).  hook() runs once every input
-  // has been read (after the first pass), before any output is emitted.
+  // has been read (after the first pass), before any output is emitted.  Each
+  // thread emits its outputs in increasing k.
   template <class Load, class Emit, class Hook>
   __device__ __forceinline__ static void run(float2* sm, const float2* tw, Load& load, Emit& emit, Hook& hook) {
     passes_from<0>(sm, tw, load, emit, hook);
