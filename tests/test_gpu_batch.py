@@ -95,3 +95,39 @@ def test_autotune_choice_cache_and_parity(torch_cuda, tmp_path):
     ora, _ = acq.search(w.x, w.chips, w.sps, w.fs_hz, w.freqs_hz, w.fft_len)
     assert n == len(ora)
     compare_detections(dets, ora)
+
+
+def test_batch_full_size_sampled(torch_cuda):
+    """The batching workload at full size (8 streams, 69 M samples, 64 codes of
+    2048-16384 chips including 2^15-point split transforms, 15-63 bins) in one
+    graph launch with autotuned plans; the oracle recomputes, bin by bin, the
+    (window, code) cells of two detections and one injected tag per stream."""
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import DETECTION_DTYPE, Batch, Search
+    wls = synth.batch()
+    cap = 4096
+    searches = [Search(w.chips, w.sps, w.fs_hz, w.freqs_hz) for w in wls]
+    xs = [torch.from_numpy(w.iq().copy()).cuda() for w in wls]
+    st = torch.cuda.current_stream()
+    for s, x, w in zip(searches, xs, wls):
+        s.autotune(st.cuda_stream, x.data_ptr(), w.n_samples, None)
+    out = torch.zeros(len(wls) * cap * 32, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(len(wls), dtype=torch.int32, device="cuda")
+    b = Batch(searches, [x.data_ptr() for x in xs], [w.n_samples for w in wls], out.data_ptr(), cap, cnt.data_ptr())
+    b.run(st.cuda_stream)
+    st.synchronize()
+    dets_all = out.cpu().numpy().view(DETECTION_DTYPE).reshape(len(wls), cap)
+    counts = cnt.cpu().numpy()
+    rng = np.random.default_rng(17)
+    for i, (w, s) in enumerate(zip(wls, searches)):
+        got = dets_all[i, :min(int(counts[i]), cap)]
+        assert len(got) > 0
+        pick = [got[j] for j in rng.choice(len(got), size=min(2, len(got)), replace=False)]
+        pairs = {(int(d["window"]), int(d["code"])) for d in pick}
+        t = w.tags[int(rng.integers(0, len(w.tags)))]
+        W, hop, N = s.windows(t.code, w.n_samples)
+        pairs.add((min(int(t.delay) // hop, W - 1), t.code))
+        ora, _ = acq.search(w.x, w.chips, w.sps, w.fs_hz, w.freqs_hz, 0, pairs=sorted(pairs))
+        sel = np.array([d for d in got if (int(d["window"]), int(d["code"])) in pairs], dtype=got.dtype)
+        compare_detections(sel, ora)
+    b.close()

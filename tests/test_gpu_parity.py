@@ -234,3 +234,38 @@ def test_realistic_full_size_sampled(torch_cuda):
     for t in wl.tags:
         assert (t.code, int(t.delay)) in found
     compare_cells(torch_cuda, wl, cells, sorted(pairs)[:6] + [(W - 1, 0)])
+
+
+def test_all_zero_stream_has_no_detections(torch_cuda):
+    """Degenerate input: every power and floor is zero; the score is defined as
+    0 (no division by zero), nothing is detected, every cell is finite."""
+    from paper_2005_10445_gb300.binding import Search
+    wl = synth.small(seed=11)
+    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len)
+    x = torch_cuda.zeros((wl.n_samples, 2), dtype=torch_cuda.float32, device="cuda")
+    dets, n, cells = s.run(x, cells=True)
+    assert n == 0
+    assert np.isfinite(cells["floor"]).all() and (cells["floor"] == 0).all()
+    assert (cells["valid"] == 1).all()
+
+
+def test_outputs_stay_inside_caller_buffers(torch_cuda):
+    """Canary bytes after the detection buffer and after the cell buffer are
+    untouched when the detections overflow the capacity."""
+    from paper_2005_10445_gb300.binding import Search
+    wl = synth.small(seed=12)
+    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len)
+    x = torch_cuda.from_numpy(wl.iq().copy()).cuda()
+    cap = 1
+    canary = 4096
+    out = torch_cuda.full((cap * 32 + canary,), 0xA5, dtype=torch_cuda.uint8, device="cuda")
+    nw = s.max_windows(wl.n_samples)
+    ncell = nw * len(wl.chips) * len(wl.freqs_hz) * 16
+    cells = torch_cuda.full((ncell + canary,), 0x5A, dtype=torch_cuda.uint8, device="cuda")
+    cnt = torch_cuda.zeros(1, dtype=torch_cuda.int32, device="cuda")
+    st = torch_cuda.cuda.current_stream()
+    s.run_cells_ptr(st.cuda_stream, x.data_ptr(), wl.n_samples, cells.data_ptr(), out.data_ptr(), cap, cnt.data_ptr())
+    st.synchronize()
+    assert int(cnt.item()) >= 3
+    assert (out[cap * 32:].cpu().numpy() == 0xA5).all()
+    assert (cells[ncell:].cpu().numpy() == 0x5A).all()
