@@ -28,10 +28,11 @@ template <int LOGM, int LOGE>
 constexpr int fft_threads() { return (1 << LOGM) >> LOGE; }
 
 // dynamic shared memory: padded transform buffer, twiddle tables of the
-// transform (and of the split stage), reduction scratch for up to 32 warps
+// transform, the 32 x 32 second-pass table, the tables of the split stage,
+// reduction scratch for up to 32 warps
 template <int LOGM>
 constexpr size_t fft_smem() {
-  return sizeof(float2) * (BlockFFT<LOGM, 5, -1>::SMEM_ELEMS + TwTables<LOGM>::N + TwTables<LOGM + 1>::N) +
+  return sizeof(float2) * (BlockFFT<LOGM, 5, -1>::SMEM_ELEMS + TwTables<LOGM>::N + 1024 + TwTables<LOGM + 1>::N) +
          32 * sizeof(float4) + sizeof(float2) * (kMaxSps + 1);
 }
 
@@ -48,11 +49,13 @@ __device__ __forceinline__ int valid_lags(const CorrParams& p, int w) {
 
 template <int LOGM, int LOGE>
 __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_window_fft(WindowFftParams p) {
-  using FFT = BlockFFT<LOGM, LOGE, -1>;
+  using FFT = BlockFFT<LOGM, LOGE, -1, true>;
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   float2* sm_tw = sm + FFT::SMEM_ELEMS;
   load_tables<LOGM>(sm_tw, p.tw);
+  __syncthreads();
+  build_tw32<LOGM>(sm_tw);
   __syncthreads();
   // every input value is read into registers/shared memory before the first
   // output is written (the passes are separated by block barriers), so the
@@ -65,11 +68,11 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_window_fft(Window
 
 template <int LOGM, int LOGE>
 __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p) {
-  using FFT = BlockFFT<LOGM, LOGE, +1>;
+  using FFT = BlockFFT<LOGM, LOGE, +1, true>;
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   float2* sm_tw = sm + FFT::SMEM_ELEMS;
-  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + TwTables<LOGM + 1>::N);
+  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + 1024 + TwTables<LOGM + 1>::N);
 
   const int rho = blockIdx.x, sps = p.sps;
   int64_t row, out;  // G row and partial-result index of this block
@@ -88,6 +91,8 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
     out = (((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho;
   }
   load_tables<LOGM>(sm_tw, p.tw);
+  __syncthreads();
+  build_tw32<LOGM>(sm_tw);
   __syncthreads();
   const int nvalid = valid_lags(p, w);
 

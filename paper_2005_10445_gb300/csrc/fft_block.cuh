@@ -147,6 +147,20 @@ struct TwTables {
 
 // W_M^t for 0 <= t < M from the shared tables (hi first, lo after), conjugated for DIR = +1.
 template <int LOGM, int DIR>
+__device__ __forceinline__ float2 twiddle(const float2* tw, int t);
+
+// W_1024^{a b} for a, b < 32 at tw[N + 32 b + a] (forward), built from the
+// two-level tables of size 2^LOGM (LOGM >= 10) already in shared memory; the
+// caller synchronises before and after.
+template <int LOGM>
+__device__ __forceinline__ void build_tw32(float2* tw) {
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+    const int a = i & 31, b = i >> 5;
+    tw[TwTables<LOGM>::N + i] = twiddle<LOGM, -1>(tw, ((a * b) & 1023) << (LOGM - 10));
+  }
+}
+
+template <int LOGM, int DIR>
 __device__ __forceinline__ float2 twiddle(const float2* tw, int t) {
   using TT = TwTables<LOGM>;
   float2 w = cmul(tw[t >> TT::LB], tw[TT::NHI + (t & (TT::NLO - 1))]);
@@ -154,7 +168,11 @@ __device__ __forceinline__ float2 twiddle(const float2* tw, int t) {
   return w;
 }
 
-template <int LOGM, int LOGE, int DIR>
+// T32: the pass over bits [5, 10) takes its twiddles W_1024^{jm r} (jm = lane,
+// r < 32) from a 32 x 32 table that follows the two-level tables in shared
+// memory ([r][jm], forward direction; see build_tw32) instead of the
+// recurrence.
+template <int LOGM, int LOGE, int DIR, bool T32 = false>
 struct BlockFFT {
   static constexpr int M = 1 << LOGM;
   static constexpr int E = 1 << LOGE;
@@ -193,7 +211,15 @@ struct BlockFFT {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const int j = t + T * s;
-      if constexpr (D > 0) {
+      if constexpr (T32 && D == 5 && RB == 5) {
+        const float2* t32 = tw + TwTables<LOGM>::N + (j & 31);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = t32[r * 32];
+          if (DIR > 0) w.y = -w.y;
+          v[s * R + r] = cmul(v[s * R + r], w);
+        }
+      } else if constexpr (D > 0) {
         // W^{jm r}: every eighth power from the tables, the others by one to
         // seven multiplications by W^{jm} (a few ulps at most)
         const int jm = j & ((1 << D) - 1);
