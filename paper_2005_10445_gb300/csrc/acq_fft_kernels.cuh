@@ -20,6 +20,8 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "acq_common.cuh"
 
 namespace atlas {
@@ -66,6 +68,10 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_window_fft(Window
   FFT::run(sm, sm_tw, load, emit);
 }
 
+// Persistent over its cells: block b takes cells b, b + gridDim.x, ...  (the
+// launch order of a one-cell-per-block grid: rho fastest, then bin, then
+// window and code), so the twiddle tables are loaded once per block and the
+// per-cell prologue is a barrier.
 template <int LOGM, int LOGE>
 __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p) {
   using FFT = BlockFFT<LOGM, LOGE, +1, true>;
@@ -74,48 +80,54 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
   float2* sm_tw = sm + FFT::SMEM_ELEMS;
   float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + 1024 + TwTables<LOGM + 1>::N);
 
-  const int rho = blockIdx.x, sps = p.sps;
-  int64_t row, out;  // G row and partial-result index of this block
-  int c, w;
-  if (p.pairs) {     // listed (G row, code, window) cells
-    const int4 pr = p.pairs[blockIdx.z];
-    row = (int64_t)pr.x * sps + rho;
-    c = pr.y;
-    w = pr.z;
-    out = (int64_t)blockIdx.z * sps + rho;
-  } else {
-    const int k = blockIdx.y, wl = blockIdx.z / p.Cg;
-    c = blockIdx.z % p.Cg;
-    w = p.w0 + wl;
-    row = ((int64_t)wl * p.K + k) * sps + rho;
-    out = (((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho;
-  }
+  const int sps = p.sps;
   load_tables<LOGM>(sm_tw, p.tw);
   __syncthreads();
   build_tw32<LOGM>(sm_tw);
-  __syncthreads();
-  const int nvalid = valid_lags(p, w);
-
-  const float2* G = p.G + row * FFT::M;
-  const float2* D = p.D + (int64_t)c * FFT::M;
-  auto load = [&](int i) { return cmul(G[i], D[i]); };
-  // lag tau = sps*q + rho is valid iff q < qlim
-  const int qlim = (nvalid - rho + sps - 1) / sps;
-  float sum = 0.f, best = -1.f;
-  int bq = 0x7fffffff;
-  // a thread's outputs arrive in increasing q: the first maximum is the smallest lag
-  auto emit = [&](int q, float2 v) {
-    const float P = fmaf(v.x, v.x, v.y * v.y);
-    sum += P;
-    if (q < qlim && P > best) {
-      best = P;
-      bq = q;
+  const int64_t n_items = p.pairs ? (int64_t)p.n_pairs * sps : (int64_t)sps * p.K * p.nw * p.Cg;
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __syncthreads();  // tables ready; the previous cell's shared-memory reads are done
+    const int rho = (int)(item % sps);
+    const int64_t rest = item / sps;
+    int64_t row, out;  // G row and partial-result index of this cell
+    int c, w;
+    if (p.pairs) {     // listed (G row, code, window) cells
+      const int4 pr = p.pairs[rest];
+      row = (int64_t)pr.x * sps + rho;
+      c = pr.y;
+      w = pr.z;
+      out = rest * sps + rho;
+    } else {
+      const int k = (int)(rest % p.K);
+      const int z = (int)(rest / p.K);
+      const int wl = z / p.Cg;
+      c = z % p.Cg;
+      w = p.w0 + wl;
+      row = ((int64_t)wl * p.K + k) * sps + rho;
+      out = (((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho;
     }
-  };
-  FFT::run(sm, sm_tw, load, emit);
-  int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
-  block_reduce_stats(sum, best, bt, red);
-  if (threadIdx.x == 0) p.part[out] = make_float4(sum, best, __int_as_float(bt), 0.f);
+    const int nvalid = valid_lags(p, w);
+    const float2* G = p.G + row * FFT::M;
+    const float2* D = p.D + (int64_t)c * FFT::M;
+    auto load = [&](int i) { return cmul(G[i], D[i]); };
+    // lag tau = sps*q + rho is valid iff q < qlim; a thread's outputs arrive in
+    // increasing q, so the first maximum is the smallest lag
+    const int qlim = (nvalid - rho + sps - 1) / sps;
+    float sum = 0.f, best = -1.f;
+    int bq = 0x7fffffff;
+    auto emit = [&](int q, float2 v) {
+      const float P = fmaf(v.x, v.x, v.y * v.y);
+      sum += P;
+      if (q < qlim && P > best) {
+        best = P;
+        bq = q;
+      }
+    };
+    FFT::run(sm, sm_tw, load, emit);
+    int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
+    block_reduce_stats(sum, best, bt, red);
+    if (threadIdx.x == 0) p.part[out] = make_float4(sum, best, __int_as_float(bt), 0.f);
+  }
 }
 
 template <int LOGH, int LOGE>
@@ -264,13 +276,32 @@ struct FftLaunch {
       return cudaGetLastError();
     }
     switch (logM) {
-      case 10: k_corr<10, LOGE><<<grid, fft_threads<10, LOGE>(), fft_smem<10>(), s>>>(p); break;
-      case 11: k_corr<11, LOGE><<<grid, fft_threads<11, LOGE>(), fft_smem<11>(), s>>>(p); break;
-      case 12: k_corr<12, LOGE><<<grid, fft_threads<12, LOGE>(), fft_smem<12>(), s>>>(p); break;
-      case 13: k_corr<13, LOGE><<<grid, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
-      case 14: k_corr<14, LOGE><<<grid, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p); break;
+      case 10: return corr_persistent<10>(p, s);
+      case 11: return corr_persistent<11>(p, s);
+      case 12: return corr_persistent<12>(p, s);
+      case 13: return corr_persistent<13>(p, s);
+      case 14: return corr_persistent<14>(p, s);
       default: return cudaErrorInvalidValue;
     }
+  }
+
+  // k_corr with as many blocks as fit on the device at once (at most one per cell)
+  template <int LOGM>
+  static cudaError_t corr_persistent(const CorrParams& p, cudaStream_t s) {
+    static int resident = 0;  // blocks resident on the whole device (computed once per process)
+    if (resident == 0) {
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_corr<LOGM, LOGE>, fft_threads<LOGM, LOGE>(),
+                                                          fft_smem<LOGM>());
+      if (e != cudaSuccess) return e;
+      resident = std::max(1, sms * std::max(per_sm, 1));
+    }
+    const int64_t items = p.pairs ? (int64_t)p.n_pairs * p.sps : (int64_t)p.sps * p.K * p.nw * p.Cg;
+    const unsigned blocks = (unsigned)std::min<int64_t>(items, resident);
+    k_corr<LOGM, LOGE><<<blocks, fft_threads<LOGM, LOGE>(), fft_smem<LOGM>(), s>>>(p);
     return cudaGetLastError();
   }
 };
