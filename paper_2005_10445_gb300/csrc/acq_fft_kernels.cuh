@@ -49,6 +49,7 @@ __device__ __forceinline__ int valid_lags(const CorrParams& p, int w) {
   return nvalid;
 }
 
+// Persistent over its rows (block b takes rows b, b + gridDim.x, ...).
 template <int LOGM, int LOGE>
 __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_window_fft(WindowFftParams p) {
   using FFT = BlockFFT<LOGM, LOGE, -1, true>;
@@ -58,14 +59,17 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_window_fft(Window
   load_tables<LOGM>(sm_tw, p.tw);
   __syncthreads();
   build_tw32<LOGM>(sm_tw);
-  __syncthreads();
-  // every input value is read into registers/shared memory before the first
-  // output is written (the passes are separated by block barriers), so the
-  // transform can overwrite its own input row
-  float2* G = p.G + (((int64_t)blockIdx.z * p.K + blockIdx.y) * p.sps + blockIdx.x) * FFT::M;
-  auto load = [&](int i) { return G[i]; };
-  auto emit = [&](int i, float2 v) { G[i] = v; };
-  FFT::run(sm, sm_tw, load, emit);
+  const int64_t rows = (int64_t)p.nw * p.K * p.sps;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    __syncthreads();  // tables ready; the previous row's shared-memory reads are done
+    // every input value is read into registers/shared memory before the first
+    // output is written (the passes are separated by block barriers), so the
+    // transform can overwrite its own input row
+    float2* G = p.G + row * FFT::M;
+    auto load = [&](int i) { return G[i]; };
+    auto emit = [&](int i, float2 v) { G[i] = v; };
+    FFT::run(sm, sm_tw, load, emit);
+  }
 }
 
 // Persistent over its cells: block b takes cells b, b + gridDim.x, ...  (the
@@ -253,13 +257,37 @@ struct FftLaunch {
       return cudaGetLastError();
     }
     switch (logM) {
-      case 10: k_window_fft<10, LOGE><<<grid, fft_threads<10, LOGE>(), fft_smem<10>(), s>>>(p); break;
-      case 11: k_window_fft<11, LOGE><<<grid, fft_threads<11, LOGE>(), fft_smem<11>(), s>>>(p); break;
-      case 12: k_window_fft<12, LOGE><<<grid, fft_threads<12, LOGE>(), fft_smem<12>(), s>>>(p); break;
-      case 13: k_window_fft<13, LOGE><<<grid, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
-      case 14: k_window_fft<14, LOGE><<<grid, fft_threads<14, LOGE>(), fft_smem<14>(), s>>>(p); break;
+      case 10: return window_persistent<10>(p, s);
+      case 11: return window_persistent<11>(p, s);
+      case 12: return window_persistent<12>(p, s);
+      case 13: return window_persistent<13>(p, s);
+      case 14: return window_persistent<14>(p, s);
       default: return cudaErrorInvalidValue;
     }
+  }
+
+  template <class K>
+  static cudaError_t resident_blocks(K kernel, int threads, size_t smem, int* out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e == cudaSuccess) *out = std::max(1, sms * std::max(per_sm, 1));
+    return e;
+  }
+
+  // k_window_fft with as many blocks as fit on the device at once (at most one per row)
+  template <int LOGM>
+  static cudaError_t window_persistent(const WindowFftParams& p, cudaStream_t s) {
+    static int resident = 0;
+    if (resident == 0) {
+      const cudaError_t e = resident_blocks(k_window_fft<LOGM, LOGE>, fft_threads<LOGM, LOGE>(), fft_smem<LOGM>(),
+                                            &resident);
+      if (e != cudaSuccess) return e;
+    }
+    const int64_t rows = (int64_t)p.nw * p.K * p.sps;
+    const unsigned blocks = (unsigned)std::min<int64_t>(rows, resident);
+    k_window_fft<LOGM, LOGE><<<blocks, fft_threads<LOGM, LOGE>(), fft_smem<LOGM>(), s>>>(p);
     return cudaGetLastError();
   }
 
@@ -290,14 +318,9 @@ struct FftLaunch {
   static cudaError_t corr_persistent(const CorrParams& p, cudaStream_t s) {
     static int resident = 0;  // blocks resident on the whole device (computed once per process)
     if (resident == 0) {
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaError_t e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_corr<LOGM, LOGE>, fft_threads<LOGM, LOGE>(),
-                                                          fft_smem<LOGM>());
+      const cudaError_t e = resident_blocks(k_corr<LOGM, LOGE>, fft_threads<LOGM, LOGE>(), fft_smem<LOGM>(),
+                                            &resident);
       if (e != cudaSuccess) return e;
-      resident = std::max(1, sms * std::max(per_sm, 1));
     }
     const int64_t items = p.pairs ? (int64_t)p.n_pairs * p.sps : (int64_t)p.sps * p.K * p.nw * p.Cg;
     const unsigned blocks = (unsigned)std::min<int64_t>(items, resident);

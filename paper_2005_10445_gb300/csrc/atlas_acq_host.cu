@@ -73,6 +73,11 @@ struct atlas_acq_ctx {
   float4* d_part = nullptr;
   size_t part_elems = 0;
   int* d_status = nullptr;
+  // the selection of a launch group runs on a side stream, overlapping the next
+  // group's mix and window transforms (its partial results are read before the
+  // next correlation overwrites them: ev_sel orders the two)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_corr = nullptr, ev_sel = nullptr;
   int wc_max = 1;  // windows per launch group (sizes the workspaces)
   // host-buffer path (allocated on first use per size, kept)
   float2* d_stage = nullptr;
@@ -170,6 +175,9 @@ void free_ctx(atlas_acq_ctx* ctx) {
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_stage_out);
   cudaFree(ctx->d_stage_count);
+  if (ctx->ev_corr) cudaEventDestroy(ctx->ev_corr);
+  if (ctx->ev_sel) cudaEventDestroy(ctx->ev_sel);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
   cudaFree(ctx->d_items);
   cudaFree(ctx->d_pairs);
   cudaFree(ctx->d_pair_stats);
@@ -248,6 +256,9 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   CK(upload(&ctx->d_inc, inc.data(), inc.size()));
   CK(cudaMalloc((void**)&ctx->d_status, sizeof(int)));
   CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+  CK(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&ctx->ev_corr, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->ev_sel, cudaEventDisableTiming));
 
   // windows per launch group: keep the window spectra of one group near L2 size
   const size_t budget = 128ull << 20;
@@ -312,8 +323,11 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
 
 // One launch group: windows [w0, w0 + nw) of group g (mix, window transforms,
 // per-code correlation, selection appending to out / d_count).
+// sel_pending: a selection of this run is in flight on the side stream (its
+// completion must be awaited before the partial results are rewritten).
 int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const float2* x, int64_t S, int W, int w0,
-                 int nw, atlas_cell* cells, atlas_detection* out, int capacity, int* d_count, bool profiling) {
+                 int nw, atlas_cell* cells, atlas_detection* out, int capacity, int* d_count, bool profiling,
+                 bool& sel_pending) {
   const int Cg = (int)g.codes.size();
   atlas::MixParams m;
   m.x = x;
@@ -357,6 +371,7 @@ int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const floa
   b.status = ctx->d_status;
   const bool timed = profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
   if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
+  if (sel_pending) CK(cudaStreamWaitEvent(st, ctx->ev_sel, 0));  // previous selection has read the partials
   if (ctx->precision != 0 && g.logM == 14 && !g.split) CK(atlas::launch_corr_tc(ctx->precision, b, st));
   else CK(atlas::launch_corr(g.logM, g.loge, g.split, b, st));
   if (timed) {
@@ -384,7 +399,11 @@ int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const floa
   c.capacity = capacity;
   c.count = d_count;
   c.cells = cells;
-  CK(atlas::launch_select(c, st));
+  CK(cudaEventRecord(ctx->ev_corr, st));
+  CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_corr, 0));
+  CK(atlas::launch_select(c, ctx->aux));
+  CK(cudaEventRecord(ctx->ev_sel, ctx->aux));
+  sel_pending = true;
   if (profiling) ctx->prof_launches += 1;
   return ATLAS_OK;
 }
@@ -420,6 +439,7 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
     for (auto& g : ctx->groups) wmax = std::max(wmax, g.windows(S));
     CK(cudaMemsetAsync(cells, 0, sizeof(atlas_cell) * (size_t)wmax * ctx->C * ctx->K, st));
   }
+  bool sel_pending = false;
   for (int gi = 0; gi < (int)ctx->groups.size(); ++gi) {
     if (only_group >= 0 && gi != only_group) continue;
     const Group& g = ctx->groups[gi];
@@ -428,10 +448,11 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
     if (g.wc > 0) wc = std::min(wc, g.wc);
     for (int w0 = 0; w0 < W; w0 += wc) {
       const int r = launch_chunk(ctx, g, st, x, S, W, w0, std::min(wc, W - w0), cells, out, capacity, d_count,
-                                 profiling);
+                                 profiling, sel_pending);
       if (r != ATLAS_OK) return r;
     }
   }
+  if (sel_pending) CK(cudaStreamWaitEvent(st, ctx->ev_sel, 0));  // every selection joins the caller's stream
   const int r = launch_refine_all(ctx, st, x, S, out, capacity, d_count);
   if (r == ATLAS_OK && profiling && capacity > 0) ctx->prof_launches += 1;
   return r;
@@ -890,15 +911,17 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
       ctx->fb_cap = cap_fb;
     }
     CK(cudaMemsetAsync(ctx->d_fb_count, 0, sizeof(int), st));
+    bool sel_pending = false;
     for (size_t i = 0; i < fallback.size();) {  // runs of consecutive windows share a launch group
       size_t j = i + 1;
       const int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)K * g.N))));
       while (j < fallback.size() && fallback[j] == fallback[j - 1] + 1 && (int)(j - i) < wc) ++j;
       r = launch_chunk(ctx, g, st, x, n_samples, W, fallback[i], (int)(j - i), nullptr, ctx->d_fb_out, cap_fb,
-                       ctx->d_fb_count, false);
+                       ctx->d_fb_count, false, sel_pending);
       if (r != ATLAS_OK) return r;
       i = j;
     }
+    if (sel_pending) CK(cudaStreamWaitEvent(st, ctx->ev_sel, 0));
     CK(cudaMemcpyAsync(&n_fb, ctx->d_fb_count, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     fb.resize(std::min(n_fb, cap_fb));
