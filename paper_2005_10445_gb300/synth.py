@@ -332,3 +332,145 @@ def proposal_stream(seed: int, n_windows: int, device, n_codes: int = 64, n_chip
         ok = idx < S
         xc.index_add_(0, idx[ok], sig[ok])
     return x, chips, freqs, truth
+
+
+# ---------------------------------------------------------------------------
+# FSK streams (Section 3: the frequency-shift-keyed transmissions of the tags,
+# received as int16 (I, Q) pairs)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class FskWorkload:
+    name: str
+    iq16: np.ndarray              # int16 [S, 2] (I, Q) pairs
+    chips: List[np.ndarray]       # +/-1 int8 per code
+    sps: int
+    fs_hz: float
+    f1_hz: float                  # tone of chip +1, relative to the band centre
+    f0_hz: float                  # tone of chip -1
+    f_lo_hz: float                # band centre relative to the receiver's centre
+    h_bp: np.ndarray              # band-pass taps (float64), an input of the search
+    fft_len: int                  # N (0 = library default per code)
+    tags: List[Tag]
+    sigma: float
+
+    @property
+    def n_samples(self) -> int:
+        return int(self.iq16.shape[0])
+
+    @property
+    def chips_concat(self) -> np.ndarray:
+        return np.concatenate(self.chips).astype(np.int8)
+
+    @property
+    def chips_per_code(self) -> np.ndarray:
+        return np.array([len(c) for c in self.chips], dtype=np.int32)
+
+
+def bandpass_taps(n_taps: int = 200, cutoff_hz: float = 1.5e6, fs_hz: float = 8e6) -> np.ndarray:
+    """A Hamming-windowed sinc low-pass of n_taps real taps: after the LO shift
+    the transmissions' band is centred at zero, so the band-pass filter of the
+    front end is a low-pass at baseband.  Unit gain at DC."""
+    n = np.arange(n_taps, dtype=np.float64)
+    t = n - (n_taps - 1) / 2.0
+    h = np.sinc(2.0 * cutoff_hz / fs_hz * t) * (0.54 - 0.46 * np.cos(2.0 * math.pi * n / (n_taps - 1)))
+    return h / h.sum()
+
+
+def fsk_transmission(chips: np.ndarray, sps: int, f1_hz: float, f0_hz: float, fs_hz: float) -> np.ndarray:
+    """Unit-amplitude continuous-phase FSK packet: chip +1 on tone f1, chip -1
+    on tone f0, sps samples per chip, phase 0 at the first sample and advanced
+    by 2 pi f / fs after each sample."""
+    f = np.where(np.repeat(np.asarray(chips) > 0, sps), f1_hz, f0_hz)
+    step = 2.0 * math.pi * f / fs_hz
+    return np.exp(1j * (np.cumsum(step) - step))
+
+
+def inject_fsk(x: np.ndarray, w: "FskWorkload", tag: Tag, amplitude: Optional[float] = None) -> None:
+    """Add one transmission at integer delay tag.delay to the complex128 stream
+    x: A exp(j(2 pi (f_lo + f_tag) t / fs + phase)) s[t - delay]."""
+    S = x.shape[0]
+    s = fsk_transmission(w.chips[tag.code], w.sps, w.f1_hz, w.f0_hz, w.fs_hz)
+    d = int(tag.delay)
+    n = min(s.shape[0], S - d)
+    if n <= 0:
+        return
+    t = d + np.arange(n, dtype=np.float64)
+    A = tag_amplitude(tag.snr_db, w.sigma) if amplitude is None else amplitude
+    x[d:d + n] += A * s[:n] * np.exp(1j * (2.0 * math.pi * (w.f_lo_hz + tag.freq_hz) * t / w.fs_hz + tag.phase))
+
+
+def quantise_iq(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest integer and saturate to int16, as [S, 2] (I, Q)."""
+    out = np.empty((x.shape[0], 2), dtype=np.int16)
+    out[:, 0] = np.clip(np.rint(x.real), -32768, 32767)
+    out[:, 1] = np.clip(np.rint(x.imag), -32768, 32767)
+    return out
+
+
+def fsk_stream(seed: int, S: int, chips: List[np.ndarray], sps: int, fs_hz: float, f1_hz: float, f0_hz: float,
+               f_lo_hz: float, n_tags: int, snr_range, offset_hz: float = 5e3, sigma: float = 2048.0,
+               n_taps: int = 200, cutoff_hz: Optional[float] = None, fft_len: int = 0,
+               min_same_code_gap: Optional[int] = None, name: str = "fsk") -> FskWorkload:
+    """Complex AWGN (sigma per component) plus n_tags FSK transmissions (code,
+    integer delay, carrier offset within +/-offset_hz of the band centre,
+    phase and SNR drawn from a seeded generator; transmissions of one code at
+    least min_same_code_gap samples apart, by default twice the window),
+    quantised to int16."""
+    rng = np.random.default_rng(seed)
+    cut = cutoff_hz if cutoff_hz is not None else 1.5 * max(abs(f1_hz), abs(f0_hz))
+    w = FskWorkload(name, np.zeros((0, 2), np.int16), chips, sps, fs_hz, f1_hz, f0_hz, f_lo_hz,
+                    bandpass_taps(n_taps, cut, fs_hz), fft_len, [], sigma)
+    z = rng.standard_normal(2 * S) * sigma
+    x = z[0::2] + 1j * z[1::2]
+    L = max(len(c) for c in chips) * sps
+    N = fft_len if fft_len else 2 * (1 << (L - 1).bit_length())
+    gap = 2 * N if min_same_code_gap is None else min_same_code_gap
+    placed: dict = {}
+    tries = 0
+    while len(w.tags) < n_tags and tries < 100000:
+        tries += 1
+        c = int(rng.integers(0, len(chips)))
+        Lc = len(chips[c]) * sps
+        if Lc > S:
+            continue
+        d = int(rng.integers(0, S - Lc + 1))
+        if any(abs(d - p) < gap for p in placed.get(c, [])):
+            continue
+        placed.setdefault(c, []).append(d)
+        tg = Tag(code=c, delay=float(d), freq_hz=float(rng.uniform(-offset_hz, offset_hz)), bin=-1,
+                 snr_db=float(rng.uniform(*snr_range)), phase=float(rng.uniform(0, 2 * math.pi)))
+        inject_fsk(x, w, tg)
+        w.tags.append(tg)
+    w.iq16 = quantise_iq(x)
+    return w
+
+
+def fsk_tiny(seed: int = 1) -> FskWorkload:
+    """16384 samples at 2 MS/s, one 1023-chip LFSR code at 2 samples/chip on
+    tones +/-500 kHz, a 200-tap band-pass filter, one tag at -5 dB."""
+    return fsk_stream(seed, 16384, [lfsr_chips(seed=seed if seed > 0 else 1)], 2, 2e6, 5e5, -5e5, 0.0, 1,
+                      (-5.0, -5.0), cutoff_hz=0.75e6, name="fsk tiny: 16384 samples, 1 code x 1023 chips, sps 2")
+
+
+def fsk_small(seed: int = 11, S: int = 40000, n_codes: int = 3, n_chips: int = 600, sps: int = 4,
+              fs_hz: float = 4e6, f_lo_hz: float = 250e3, n_tags: int = 4, fft_len: int = 0,
+              snr_range=(-8.0, 0.0)) -> FskWorkload:
+    """A few ragged windows, several codes, an LO offset."""
+    chips = [random_chips(n_chips, seed * 1_000_003 + c) for c in range(n_codes)]
+    return fsk_stream(seed, S, chips, sps, fs_hz, 5e5, -5e5, f_lo_hz, n_tags, snr_range, fft_len=fft_len,
+                      name=f"fsk small: {S} samples, {n_codes} codes x {n_chips} chips, sps {sps}")
+
+
+def fsk_realistic(seed: int = 2, seconds: float = 1.0, n_codes: int = 16, n_chips: int = 8192, sps: int = 8,
+                  fs_hz: float = 8e6, f_lo_hz: float = 1e6, n_tags: int = 40, snr_range=(-15.0, 0.0),
+                  chip_lengths: Optional[Sequence[int]] = None) -> FskWorkload:
+    """1 s at 8 MS/s of int16 samples, 16 codes x 8192 chips at 8 samples/chip
+    on tones +/-500 kHz around a band centre 1 MHz off the receiver's, a
+    200-tap band-pass filter, 40 tags with SNR U[-15, 0] dB.  chip_lengths
+    (optional) gives each code its own length."""
+    S = int(round(seconds * fs_hz))
+    lens = list(chip_lengths) if chip_lengths is not None else [n_chips] * n_codes
+    chips = [random_chips(n, seed * 1_000_003 + c) for c, n in enumerate(lens)]
+    return fsk_stream(seed, S, chips, sps, fs_hz, 5e5, -5e5, f_lo_hz, n_tags, snr_range,
+                      name=f"fsk realistic: {S} samples at {fs_hz/1e6:g} MS/s, {len(chips)} codes, sps {sps}")
