@@ -1,0 +1,147 @@
+/*
+ * atlas_fsk.h -- C ABI of the FSK acquisition front end.
+ *
+ * The front end of Section 3 (steps 1-8, stated there for frequency-shift
+ * keying) with the filter composition and cross-correlation identity of
+ * Section 4.1.  For a stream of int16 (I, Q) pairs:
+ *
+ *   1. x[i] = I[i] + j Q[i]
+ *   2. x[i] <- x[i] * exp(-j 2 pi f_lo i / fs)          (i: absolute sample index)
+ *   3-4. f_b[i] = sum_{t<T} g_b[t] x[i-t], x[i<0] = 0, b in {1, 0}, with the
+ *        composed filters g_b = h_bp * m_b (band-pass, then the matched filter
+ *        of one chip of tone f_b: m_b[t] = exp(-j 2 pi f_b (sps-1-t) / fs))
+ *   5. d = (|f_1| - |f_0|) / (|f_1| + |f_0|) (0 where both vanish), u = |f_1| - |f_0|;
+ *      d and u have the stream's length (zero at and past its end)
+ *   6. the same steps (no LO mix) on the replica of each code -- a
+ *      continuous-phase FSK packet, chip +1 on tone f_1, chip -1 on tone f_0,
+ *      phase 0 at its first sample -- give d_c, nonzero on n_c = L + T - 1
+ *      samples (L = chips * sps)
+ *   7. per overlapping window w (hop = N - n_c, window w covers samples
+ *      [w hop, w hop + N)): corr[tau] = sum_{n<n_c} d_c[n] d[w hop + (tau+n) mod N]
+ *   8. j = argmax over the window's valid lags of |corr| (smallest on ties);
+ *      score = corr[j]^2 / mean_{tau<N} corr[tau]^2; a detection when
+ *      score >= threshold, with w_c = sum d_c[n] d[a+n], q = sum d[a+n]^2,
+ *      p_c = sum d_c[n] u[a+n] (n < n_c, a = w hop + j, direct FP64 sums) and
+ *      the arrival time a + delta, delta the vertex of the parabola through
+ *      corr^2 at a-1, a, a+1 (0 at the stream ends).
+ *
+ * Valid lags: [0, hop) in every window but the last, [0, min(hop, S - n_c -
+ * w hop)] in the last, so every absolute lag 0 .. S - n_c is searched once.
+ *
+ * Threading, streams and errors as for atlas_acq.h (ATLAS_OK or a negative
+ * ATLAS_ERR_* code; atlas_fsk_last_error() after ATLAS_ERR_CUDA).
+ */
+#ifndef ATLAS_FSK_H_
+#define ATLAS_FSK_H_
+
+#include <stdint.h>
+
+#include "atlas_acq.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct atlas_fsk_ctx* atlas_fsk_t;
+
+/* One FSK detection (48 bytes), written into caller-owned memory. */
+typedef struct {
+  int32_t code;    /* code index */
+  int32_t window;  /* window index w; the window starts at sample w * hop_c */
+  int32_t lag;     /* window-relative lag j; absolute lag a = window * hop_c + lag */
+  float   score;   /* corr[j]^2 / floor (FP32 transform path) */
+  double  toa;     /* a + delta, samples from the stream start */
+  double  w_c;     /* sum_n d_c[n] d[a+n]  (FP64 sums of the FP32 d, u, d_c) */
+  double  q;       /* sum_n d[a+n]^2 */
+  double  p_c;     /* sum_n d_c[n] u[a+n] */
+} atlas_fsk_detection;
+
+typedef struct {
+  float   threshold;          /* on corr[j]^2 / floor; default 49 */
+  int32_t fft_len;            /* N for every code; 0 = 2 * nextpow2(L_c) per code */
+  int32_t windows_per_launch; /* windows per launch group, rounded up to an even count; 0 = 64 */
+  int32_t reserved[5];
+} atlas_fsk_opts;
+
+void atlas_fsk_default_opts(atlas_fsk_opts* opts);
+
+/*
+ * Create an FSK search context on the current CUDA device.
+ *   chips, chips_per_code, n_codes  as atlas_acq_create (host, +/-1 int8, copied)
+ *   samples_per_chip  sps >= 1
+ *   fs_hz             sample rate (> 0)
+ *   f1_hz, f0_hz      tones of chips +1 and -1, relative to the band centre
+ *   f_lo_hz           band centre relative to the receiver's centre (step 2)
+ *   h_bp              host, [n_bp][2] double (re, im) band-pass taps (copied)
+ *   n_bp              1 .. 1024 - sps + 1 (the composed filters have T = n_bp + sps - 1 taps)
+ * Composes the filters in FP64 on the host, transforms them, builds every
+ * code's replica, d_c and stored conjugated spectrum on the device (Section
+ * 4.2: computed once and kept), allocates the workspaces and synchronises.
+ * Supported: N a power of two, 2^10 .. 2^17, N > n_c; otherwise
+ * ATLAS_ERR_UNSUPPORTED.  *out is released with atlas_fsk_destroy().
+ */
+int atlas_fsk_create(atlas_fsk_t* out, const int8_t* chips, const int32_t* chips_per_code, int32_t n_codes,
+                     int32_t samples_per_chip, double fs_hz, double f1_hz, double f0_hz, double f_lo_hz,
+                     const double* h_bp, int32_t n_bp, const atlas_fsk_opts* opts);
+
+/* Plan of code `code` for n_samples (no device work): window count, hop,
+ * transform length N and the support n_c of d_c. */
+int atlas_fsk_windows(atlas_fsk_t ctx, int32_t code, int64_t n_samples, int32_t* n_windows, int32_t* hop,
+                      int32_t* fft_len, int32_t* support);
+
+/*
+ * Run the search on a device-resident stream.
+ *   stream     cudaStream_t (as void*); NULL = the legacy default stream
+ *   d_iq       device, [n_samples][2] int16 (I, Q), caller-owned
+ *   n_samples  S >= the largest support n_c
+ *   d_out      device, [capacity] atlas_fsk_detection, caller-owned
+ *   d_count    device, one int32: the number of detections (may exceed capacity;
+ *              only the first `capacity` records are written)
+ * Detections are ordered by (code length group, window, code).  Asynchronous
+ * and stream-ordered; allocates nothing.
+ */
+int atlas_fsk_run(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t n_samples,
+                  atlas_fsk_detection* d_out, int32_t capacity, int32_t* d_count);
+
+/* The same with host buffers: copies h_iq in, searches, copies the records and
+ * the count out, and synchronises.  Device staging buffers are allocated on
+ * first use for a size and kept. */
+int atlas_fsk_run_host(atlas_fsk_t ctx, void* stream, const int16_t* h_iq, int64_t n_samples,
+                       atlas_fsk_detection* h_out, int32_t capacity, int32_t* h_count);
+
+/* Steps 1-5 alone: d and u of stream indices [start, start + count) into the
+ * device arrays d_d and d_u (caller-owned, `count` floats each; d_u may be
+ * NULL).  For inspection and testing. */
+int atlas_fsk_demod(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t n_samples, int64_t start,
+                    int64_t count, float* d_d, float* d_u);
+
+/* Copy code `code`'s stored d_c (n_c floats) to host memory h_dc of `cap`
+ * floats; *n gets n_c. */
+int atlas_fsk_code_demod(atlas_fsk_t ctx, int32_t code, float* h_dc, int32_t cap, int32_t* n);
+
+/* Device-time profile of the runs between begin and end: CUDA events on the
+ * run's stream around the demodulation and correlation launches (at most
+ * max_timed of each kind are timed; the counts cover every launch). */
+typedef struct {
+  int64_t launches;        /* kernels the profiled runs launched */
+  int64_t corr_launches;   /* correlation launches (inverse transform, corr^2, floor, argmax) */
+  int64_t corr_units;      /* (window, code) cells they processed */
+  int64_t corr_timed;
+  double  corr_ms;         /* summed device time of the timed correlation launches */
+  int64_t demod_launches;  /* demodulation launches (steps 1-5) */
+  int64_t demod_samples;   /* samples they demodulated */
+  int64_t demod_timed;
+  double  demod_ms;        /* summed device time of the timed demodulation launches */
+} atlas_fsk_profile;
+
+int atlas_fsk_profile_begin(atlas_fsk_t ctx, int32_t max_timed);
+int atlas_fsk_profile_end(atlas_fsk_t ctx, atlas_fsk_profile* out);
+
+const char* atlas_fsk_last_error(atlas_fsk_t ctx);
+void atlas_fsk_destroy(atlas_fsk_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATLAS_FSK_H_ */

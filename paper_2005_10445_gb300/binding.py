@@ -36,6 +36,12 @@ EXPORTED = [
     "atlas_prop_features", "atlas_prop_loss_grad", "atlas_prop_adam", "atlas_prop_logits", "atlas_prop_candidates",
     "atlas_acq_run_proposed", "atlas_prop_last_error", "atlas_prop_destroy",
 ]
+# Every symbol include/atlas_fsk.h declares.
+EXPORTED_FSK = [
+    "atlas_fsk_default_opts", "atlas_fsk_create", "atlas_fsk_windows", "atlas_fsk_run", "atlas_fsk_run_host",
+    "atlas_fsk_demod", "atlas_fsk_code_demod", "atlas_fsk_profile_begin", "atlas_fsk_profile_end",
+    "atlas_fsk_last_error", "atlas_fsk_destroy",
+]
 
 
 class Detection(ctypes.Structure):
@@ -59,6 +65,27 @@ class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("corr_launches", ctypes.c_int64), ("corr_ms", ctypes.c_double),
                 ("corr_units", ctypes.c_int64), ("timed_launches", ctypes.c_int64)]
 
+
+class FskDetection(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("window", ctypes.c_int32), ("lag", ctypes.c_int32),
+                ("score", ctypes.c_float), ("toa", ctypes.c_double), ("w_c", ctypes.c_double),
+                ("q", ctypes.c_double), ("p_c", ctypes.c_double)]
+
+
+class FskOpts(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_float), ("fft_len", ctypes.c_int32),
+                ("windows_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class FskProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("corr_launches", ctypes.c_int64), ("corr_units", ctypes.c_int64),
+                ("corr_timed", ctypes.c_int64), ("corr_ms", ctypes.c_double), ("demod_launches", ctypes.c_int64),
+                ("demod_samples", ctypes.c_int64), ("demod_timed", ctypes.c_int64), ("demod_ms", ctypes.c_double)]
+
+
+FSK_DETECTION_DTYPE = np.dtype([("code", "<i4"), ("window", "<i4"), ("lag", "<i4"), ("score", "<f4"),
+                                ("toa", "<f8"), ("w_c", "<f8"), ("q", "<f8"), ("p_c", "<f8")])
+assert FSK_DETECTION_DTYPE.itemsize == ctypes.sizeof(FskDetection) == 48
 
 DETECTION_DTYPE = np.dtype([("code", "<i4"), ("window", "<i4"), ("lag", "<i4"), ("freq_bin", "<i4"),
                             ("score", "<f4"), ("peak_power", "<f4"), ("toa", "<f8")])
@@ -146,6 +173,29 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_prop_last_error.restype = ctypes.c_char_p
     lib.atlas_prop_destroy.argtypes = [vp]
     lib.atlas_prop_destroy.restype = None
+    lib.atlas_fsk_default_opts.argtypes = [ctypes.POINTER(FskOpts)]
+    lib.atlas_fsk_default_opts.restype = None
+    lib.atlas_fsk_create.argtypes = [ctypes.POINTER(vp), vp, vp, i32, i32, f64, f64, f64, f64, vp, i32,
+                                     ctypes.POINTER(FskOpts)]
+    lib.atlas_fsk_create.restype = ctypes.c_int
+    lib.atlas_fsk_windows.argtypes = [vp, i32, i64] + [ctypes.POINTER(i32)] * 4
+    lib.atlas_fsk_windows.restype = ctypes.c_int
+    lib.atlas_fsk_run.argtypes = [vp, vp, vp, i64, vp, i32, vp]
+    lib.atlas_fsk_run.restype = ctypes.c_int
+    lib.atlas_fsk_run_host.argtypes = [vp, vp, vp, i64, vp, i32, vp]
+    lib.atlas_fsk_run_host.restype = ctypes.c_int
+    lib.atlas_fsk_demod.argtypes = [vp, vp, vp, i64, i64, i64, vp, vp]
+    lib.atlas_fsk_demod.restype = ctypes.c_int
+    lib.atlas_fsk_code_demod.argtypes = [vp, i32, vp, i32, ctypes.POINTER(i32)]
+    lib.atlas_fsk_code_demod.restype = ctypes.c_int
+    lib.atlas_fsk_profile_begin.argtypes = [vp, i32]
+    lib.atlas_fsk_profile_begin.restype = ctypes.c_int
+    lib.atlas_fsk_profile_end.argtypes = [vp, ctypes.POINTER(FskProfile)]
+    lib.atlas_fsk_profile_end.restype = ctypes.c_int
+    lib.atlas_fsk_last_error.argtypes = [vp]
+    lib.atlas_fsk_last_error.restype = ctypes.c_char_p
+    lib.atlas_fsk_destroy.argtypes = [vp]
+    lib.atlas_fsk_destroy.restype = None
     lib.atlas_acq_strerror.argtypes = [ctypes.c_int]
     lib.atlas_acq_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -408,3 +458,113 @@ def run_proposed(search: "Search", prop: Proposal, stream: int, d_iq: int, n_sam
     _check(load().atlas_acq_run_proposed(search.ctx, prop.p, stream, d_iq, n_samples, topk, float(tau_fb), d_out,
                                          capacity, d_count, ctypes.byref(nfb)), search.ctx)
     return nfb.value
+
+
+# ---------------------------------------------------------------------------
+# FSK front end (include/atlas_fsk.h)
+# ---------------------------------------------------------------------------
+
+def _check_fsk(status: int, ctx=None) -> None:
+    if status != ATLAS_OK:
+        msg = strerror(status)
+        if ctx is not None and status == ATLAS_ERR_CUDA:
+            msg += ": " + load().atlas_fsk_last_error(ctx).decode()
+        raise AtlasError(status, msg)
+
+
+class FskSearch:
+    """An FSK search context (atlas_fsk_create / atlas_fsk_destroy)."""
+
+    def __init__(self, chips: Sequence[np.ndarray], samples_per_chip: int, fs_hz: float, f1_hz: float,
+                 f0_hz: float, f_lo_hz: float, h_bp: np.ndarray, threshold: float = 49.0, fft_len: int = 0,
+                 windows_per_launch: int = 0):
+        lib = load()
+        self._lib = lib
+        self.ctx = ctypes.c_void_p()
+        cat = np.ascontiguousarray(np.concatenate([np.asarray(c, np.int8) for c in chips]))
+        cpc = np.ascontiguousarray(np.array([len(c) for c in chips], np.int32))
+        h = np.asarray(h_bp)
+        taps = np.ascontiguousarray(np.stack([h.real, h.imag], axis=-1).astype(np.float64)) \
+            if np.iscomplexobj(h) else np.ascontiguousarray(
+                np.stack([h.astype(np.float64), np.zeros(h.shape[0])], axis=-1))
+        o = FskOpts()
+        lib.atlas_fsk_default_opts(ctypes.byref(o))
+        o.threshold = threshold
+        o.fft_len = fft_len
+        o.windows_per_launch = windows_per_launch
+        self.n_codes = len(chips)
+        st = lib.atlas_fsk_create(ctypes.byref(self.ctx), cat.ctypes.data, cpc.ctypes.data, len(chips),
+                                  samples_per_chip, float(fs_hz), float(f1_hz), float(f0_hz), float(f_lo_hz),
+                                  taps.ctypes.data, taps.shape[0], ctypes.byref(o))
+        if st != ATLAS_OK:
+            self.ctx = None
+        _check_fsk(st)
+
+    def close(self) -> None:
+        if self.ctx:
+            self._lib.atlas_fsk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def windows(self, code: int, n_samples: int):
+        """(W, hop, N, n_c) of a code."""
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check_fsk(self._lib.atlas_fsk_windows(self.ctx, code, n_samples, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def run_ptr(self, stream: int, d_iq: int, n_samples: int, d_out: int, capacity: int, d_count: int) -> None:
+        _check_fsk(self._lib.atlas_fsk_run(self.ctx, stream, d_iq, n_samples, d_out, capacity, d_count), self.ctx)
+
+    def run_host_ptr(self, stream: int, h_iq: int, n_samples: int, h_out: int, capacity: int,
+                     h_count: int) -> None:
+        _check_fsk(self._lib.atlas_fsk_run_host(self.ctx, stream, h_iq, n_samples, h_out, capacity, h_count),
+                   self.ctx)
+
+    def demod_ptr(self, stream: int, d_iq: int, n_samples: int, start: int, count: int, d_d: int,
+                  d_u: int = 0) -> None:
+        _check_fsk(self._lib.atlas_fsk_demod(self.ctx, stream, d_iq, n_samples, start, count, d_d, d_u or None),
+                   self.ctx)
+
+    def code_demod(self, code: int) -> np.ndarray:
+        n = ctypes.c_int32()
+        _check_fsk(self._lib.atlas_fsk_code_demod(self.ctx, code, None, 0, ctypes.byref(n)), self.ctx)
+        out = np.zeros(n.value, np.float32)
+        _check_fsk(self._lib.atlas_fsk_code_demod(self.ctx, code, out.ctypes.data, n.value, ctypes.byref(n)),
+                   self.ctx)
+        return out
+
+    def profile_begin(self, max_timed: int = 65536) -> None:
+        _check_fsk(self._lib.atlas_fsk_profile_begin(self.ctx, max_timed), self.ctx)
+
+    def profile_end(self) -> dict:
+        p = FskProfile()
+        _check_fsk(self._lib.atlas_fsk_profile_end(self.ctx, ctypes.byref(p)), self.ctx)
+        return {f: getattr(p, f) for f, _ in FskProfile._fields_}
+
+    # torch conveniences ---------------------------------------------------
+    def run(self, iq, capacity: int = 4096, stream=None):
+        """iq: torch CUDA int16 tensor [S, 2].  Returns (detections as a numpy
+        structured array, count)."""
+        import torch
+        assert iq.is_cuda and iq.dtype == torch.int16 and iq.is_contiguous()
+        S = iq.shape[0]
+        out = torch.zeros(max(capacity, 1) * FSK_DETECTION_DTYPE.itemsize, dtype=torch.uint8, device=iq.device)
+        cnt = torch.zeros(1, dtype=torch.int32, device=iq.device)
+        st = stream if stream is not None else torch.cuda.current_stream(iq.device).cuda_stream
+        self.run_ptr(st, iq.data_ptr(), S, out.data_ptr(), capacity, cnt.data_ptr())
+        torch.cuda.current_stream(iq.device).synchronize() if stream is None else None
+        n = int(cnt.item())
+        dets = out.cpu().numpy().view(FSK_DETECTION_DTYPE)[: min(n, capacity)].copy()
+        return dets, n
+
+    def run_host(self, iq16: np.ndarray, capacity: int = 4096, stream: int = 0):
+        a = np.ascontiguousarray(iq16, dtype=np.int16)
+        out = np.zeros(max(capacity, 1), FSK_DETECTION_DTYPE)
+        cnt = ctypes.c_int32()
+        self.run_host_ptr(stream, a.ctypes.data, a.shape[0], out.ctypes.data, capacity, ctypes.addressof(cnt))
+        return out[: min(cnt.value, capacity)].copy(), cnt.value

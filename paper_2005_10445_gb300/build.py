@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libatlas_acq.so")
-SOURCES = ["acq_kernels.cu", "acq_fft_e4.cu", "acq_fft_e5.cu", "atlas_acq_host.cu", "acq_static.cu", "prop_kernels.cu", "acq_tc.cu"]
+SOURCES = ["acq_kernels.cu", "acq_fft_e4.cu", "acq_fft_e5.cu", "atlas_acq_host.cu", "acq_static.cu", "prop_kernels.cu",
+           "acq_tc.cu", "fsk_kernels.cu", "fsk_fft.cu", "atlas_fsk_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -40,7 +41,7 @@ def _newer(target: str, deps) -> bool:
 def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(INCLUDE, "atlas_acq.h"))
+    headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     objs = []
     jobs = []
     for src in SOURCES:

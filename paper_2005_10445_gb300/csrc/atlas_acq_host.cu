@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "acq_internal.h"
+#include "host_util.h"
 #include "atlas_acq.h"
 #include "prop_internal.h"
 
@@ -24,6 +25,37 @@ using atlas::CorrParams;
 using atlas::RefineParams;
 using atlas::SelectParams;
 using atlas::WindowFftParams;
+
+namespace atlas {
+
+// turns * 2^64 of f/fs, reduced to [-1/2, 1/2) turns, as two's complement.
+uint64_t phase_increment(double f_hz, double fs_hz) {
+  double t = f_hz / fs_hz;
+  t -= nearbyint(t);
+  if (t >= 0.5) t -= 1.0;
+  const double scaled = ldexp(t, 64);
+  return (uint64_t)(int64_t)llrint(scaled);
+}
+
+// W_M^t = exp(-2 pi i t / M): HI[i] = W^{i << LB}, LO[i] = W^i, FP64 then rounded.
+std::vector<float2> twiddle_tables(int logM) {
+  const int LB = logM / 2, HB = logM - LB;
+  const int nlo = 1 << LB, nhi = 1 << HB;
+  const double M = (double)(1 << logM);
+  std::vector<float2> t(nlo + nhi);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int i = 0; i < nhi; ++i) {
+    const double a = -two_pi * (double)((int64_t)i << LB) / M;
+    t[i] = make_float2((float)cos(a), (float)sin(a));
+  }
+  for (int i = 0; i < nlo; ++i) {
+    const double a = -two_pi * (double)i / M;
+    t[nhi + i] = make_float2((float)cos(a), (float)sin(a));
+  }
+  return t;
+}
+
+}  // namespace atlas
 
 namespace {
 
@@ -127,32 +159,8 @@ int ilog2(int64_t v) {
   return r;
 }
 
-// turns * 2^64 of f/fs, reduced to [-1/2, 1/2) turns, as two's complement.
-uint64_t phase_increment(double f_hz, double fs_hz) {
-  double t = f_hz / fs_hz;
-  t -= nearbyint(t);
-  if (t >= 0.5) t -= 1.0;
-  const double scaled = ldexp(t, 64);
-  return (uint64_t)(int64_t)llrint(scaled);
-}
-
-// W_M^t = exp(-2 pi i t / M): HI[i] = W^{i << LB}, LO[i] = W^i, FP64 then rounded.
-std::vector<float2> twiddle_tables(int logM) {
-  const int LB = logM / 2, HB = logM - LB;
-  const int nlo = 1 << LB, nhi = 1 << HB;
-  const double M = (double)(1 << logM);
-  std::vector<float2> t(nlo + nhi);
-  const double two_pi = 6.283185307179586476925286766559;
-  for (int i = 0; i < nhi; ++i) {
-    const double a = -two_pi * (double)((int64_t)i << LB) / M;
-    t[i] = make_float2((float)cos(a), (float)sin(a));
-  }
-  for (int i = 0; i < nlo; ++i) {
-    const double a = -two_pi * (double)i / M;
-    t[nhi + i] = make_float2((float)cos(a), (float)sin(a));
-  }
-  return t;
-}
+using atlas::phase_increment;
+using atlas::twiddle_tables;
 
 void free_ctx(atlas_acq_ctx* ctx) {
   if (!ctx) return;

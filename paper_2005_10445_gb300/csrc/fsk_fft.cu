@@ -1,0 +1,281 @@
+// fsk_fft.cu -- the N-point transforms of the FSK cross-correlation (Section 3
+// step 7, computed with FFTs as in Section 4.1).  N = R * M: M <= 2^14 points
+// live in one block's shared memory and R in {1, 2, 4, 8} blocks of a
+// thread-block cluster exchange through distributed shared memory, so a
+// transform of up to 2^17 points never goes through global memory.
+//
+// Index maps (n = m + M n2, k = R k2 + r with m, k2 < M and n2, r < R):
+//   forward   X[R k2 + r] = sum_m W_M^{m k2} ( W_N^{m r} sum_n2 x[m + M n2] W_R^{n2 r} )
+//     Block rho of the cluster takes the m of its range [rho M/R, (rho+1) M/R),
+//     forms the R-point DFT of the values M apart, multiplies value r by
+//     W_N^{m r} and stores it at position m of block r's shared memory.  After
+//     a cluster barrier block r runs the M-point block FFT and writes the run
+//     X_perm[r M + k2] = X[R k2 + r] (the "permuted" spectrum: each block
+//     writes one contiguous run).
+//   inverse   z[m + M n2] = sum_r W_R^{-n2 r} ( W_N^{-m r} sum_k2 Z[R k2 + r] W_M^{-m k2} )
+//     Block r inverse-transforms its run Z_perm[r M + .] with the block FFT,
+//     multiplies by W_N^{-m r} and keeps the values in its shared memory.
+//     After a cluster barrier block rho reads, for each m of its range, the
+//     R values at m from the R blocks and takes the R-point DFT across them:
+//     the lags m + M n2.
+// Window and code spectra share the permuted layout, so the pointwise product
+// of the correlation needs no reordering.
+//
+// Real inputs are packed two per transform: the forward transform takes
+// x = d_w + j d_{w+1} (two windows of the real demodulated stream); with the
+// code spectra conj(DFT(d_c)) / N, the inverse transform of X * C gives
+// corr_w + j corr_{w+1}.
+#include <cooperative_groups.h>
+#include <limits.h>
+
+#include "acq_common.cuh"
+#include "fsk_internal.h"
+
+namespace atlas {
+namespace cg = cooperative_groups;
+
+template <int LOGM>
+constexpr int fsk_fft_threads() { return (1 << LOGM) >> kLogE; }
+
+// padded transform buffer, tables of M and of N, reduction scratch (2 x 32)
+template <int LOGM, int LOGN>
+constexpr size_t fsk_fft_smem() {
+  return sizeof(float2) * (BlockFFT<LOGM, kLogE, -1>::SMEM_ELEMS + TwTables<LOGM>::N + TwTables<LOGN>::N) +
+         64 * sizeof(float4);
+}
+
+// The passes of a block FFT whose input is already in shared memory (natural
+// index i at spad(i)).
+template <class FFT, int LOGM, int D, class Emit>
+__device__ __forceinline__ void passes_from_shared(float2* sm, const float2* tw, Emit& emit) {
+  constexpr int RB = (LOGM - D) < kLogE ? (LOGM - D) : kLogE;
+  constexpr bool LAST = (D + RB == LOGM);
+  auto none = [](int) { return make_float2(0.f, 0.f); };
+  FFT::template pass<D, RB, false, LAST>(sm, tw, none, emit);
+  if constexpr (!LAST) passes_from_shared<FFT, LOGM, D + RB>(sm, tw, emit);
+}
+
+// value n of item `item`'s real sequence `which` (0: real part, 1: imaginary)
+__device__ __forceinline__ float fsk_fwd_value(const FskFwdParams& p, int item, int which, int n) {
+  if (p.rows) {
+    if (which) return 0.f;
+    return n < p.n_valid ? p.rows[(int64_t)item * p.ld + n] : 0.f;
+  }
+  const int wl = 2 * item + which;
+  if (wl >= p.nw) return 0.f;
+  const int64_t i = (int64_t)(p.w0 + wl) * p.hop + n - p.base;
+  return (i >= 0 && i < p.len) ? p.d[i] : 0.f;
+}
+
+template <int LOGM, int R>
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>()) k_fsk_fwd(FskFwdParams p) {
+  using FFT = BlockFFT<LOGM, kLogE, -1>;
+  constexpr int M = 1 << LOGM;
+  constexpr int N = M * R;
+  constexpr int LOGN = LOGM + ct_log2(R);
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  float2* sm_twN = sm_tw + TwTables<LOGM>::N;
+  load_tables<LOGM>(sm_tw, p.tw);
+  if constexpr (R > 1) load_tables<LOGN>(sm_twN, p.twN);
+  const int item = blockIdx.x / R;
+  const int rank = blockIdx.x % R;  // the block's rank in its cluster of R
+  float2* X = p.X + (int64_t)item * N + (int64_t)rank * M;
+  const float sc = p.scale;
+  const float sy = p.conj_out ? -sc : sc;
+  auto emit = [&](int k, float2 v) { X[k] = make_float2(v.x * sc, v.y * sy); };
+  __syncthreads();  // tables
+  if constexpr (R == 1) {
+    auto load = [&](int n) { return make_float2(fsk_fwd_value(p, item, 0, n), fsk_fwd_value(p, item, 1, n)); };
+    FFT::run(sm, sm_tw, load, emit);
+  } else {
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();  // every block of the cluster runs before the first remote store
+    constexpr int MR = M / R;
+    float2* dst[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r] = cluster.map_shared_rank(sm, r);
+    for (int j = threadIdx.x; j < MR; j += blockDim.x) {
+      const int m = rank * MR + j;
+      float2 v[R];
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2)
+        v[n2] = make_float2(fsk_fwd_value(p, item, 0, m + M * n2), fsk_fwd_value(p, item, 1, m + M * n2));
+      dft_reg<R, -1>(v);
+      dst[0][spad(m)] = v[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) dst[r][spad(m)] = cmul(v[r], twiddle<LOGN, -1>(sm_twN, m * r));
+    }
+    cluster.sync();  // every block's M values are in place
+    passes_from_shared<FFT, LOGM, 0>(sm, sm_tw, emit);
+  }
+}
+
+// valid lags of window w (the overlap rule with the support n_c)
+__device__ __forceinline__ int fsk_valid_lags(const FskCorrParams& p, int w) {
+  if (w < p.W - 1) return p.hop;
+  const int64_t lim = p.S - p.n_c - (int64_t)w * p.hop;
+  return (int)(lim < p.hop ? lim : p.hop) + 1;
+}
+
+template <int LOGM, int R>
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>()) k_fsk_corr(FskCorrParams p) {
+  using FFT = BlockFFT<LOGM, kLogE, +1>;
+  constexpr int M = 1 << LOGM;
+  constexpr int N = M * R;
+  constexpr int LOGN = LOGM + ct_log2(R);
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  float2* sm_twN = sm_tw + TwTables<LOGM>::N;
+  float4* red = reinterpret_cast<float4*>(sm_twN + TwTables<LOGN>::N);
+  load_tables<LOGM>(sm_tw, p.tw);
+  if constexpr (R > 1) load_tables<LOGN>(sm_twN, p.twN);
+  const int item = blockIdx.x / R;
+  const int rank = blockIdx.x % R;
+  const int pr = item / p.Cg, c = item % p.Cg;
+  const int wl0 = 2 * pr, wl1 = 2 * pr + 1;
+  const bool has1 = wl1 < p.nw;
+  const int nv0 = fsk_valid_lags(p, p.w0 + wl0);
+  const int nv1 = has1 ? fsk_valid_lags(p, p.w0 + wl1) : 0;
+  const float2* X = p.X + (int64_t)pr * N + (int64_t)rank * M;
+  const float2* C = p.C + (int64_t)c * N + (int64_t)rank * M;
+  auto load = [&](int k) { return cmul(X[k], C[k]); };
+  float s0 = 0.f, b0 = -1.f, s1 = 0.f, b1 = -1.f;
+  int t0 = INT_MAX, t1 = INT_MAX;
+  auto take = [&](int tau, float2 z) {
+    const float P0 = z.x * z.x, P1 = z.y * z.y;
+    s0 += P0;
+    s1 += P1;
+    if (tau < nv0) better(b0, t0, P0, tau);
+    if (tau < nv1) better(b1, t1, P1, tau);
+  };
+  __syncthreads();  // tables
+  if constexpr (R == 1) {
+    auto emit = [&](int m, float2 v) { take(m, v); };
+    FFT::run(sm, sm_tw, load, emit);
+  } else {
+    // the last pass has read all of its inputs (block barrier) before it
+    // emits, so the outputs can go back into the same buffer
+    auto emit = [&](int m, float2 v) { sm[spad(m)] = cmul(v, twiddle<LOGN, +1>(sm_twN, m * rank)); };
+    FFT::run(sm, sm_tw, load, emit);
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();  // every block's inverse transform is in its shared memory
+    constexpr int MR = M / R;
+    const float2* src[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) src[r] = cluster.map_shared_rank(sm, r);
+    for (int j = threadIdx.x; j < MR; j += blockDim.x) {
+      const int m = rank * MR + j;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = src[r][spad(m)];
+      dft_reg<R, +1>(v);
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2) take(m + M * n2, v[n2]);
+    }
+    cluster.sync();  // no block leaves while another still reads its shared memory
+  }
+  block_reduce_stats(s0, b0, t0, red);
+  block_reduce_stats(s1, b1, t1, red + 32);
+  if (threadIdx.x == 0) {
+    p.part[((int64_t)wl0 * p.Cg + c) * R + rank] = make_float4(s0, b0, __int_as_float(t0), 0.f);
+    if (has1) p.part[((int64_t)wl1 * p.Cg + c) * R + rank] = make_float4(s1, b1, __int_as_float(t1), 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+namespace {
+
+template <int LOGM, int R>
+cudaError_t prepare_one() {
+  constexpr int LOGN = LOGM + ct_log2(R);
+  cudaError_t e = cudaFuncSetAttribute(k_fsk_fwd<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fsk_fft_smem<LOGM, LOGN>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fsk_fft_smem<LOGM, LOGN>());
+}
+
+template <class P>
+cudaError_t launch_clustered(void (*kern)(P), int R, int blocks, int threads, size_t smem, const P& p,
+                             cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = R;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = R > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+template <int LOGM, int R>
+cudaError_t fwd_one(const FskFwdParams& p, cudaStream_t s) {
+  constexpr int LOGN = LOGM + ct_log2(R);
+  return launch_clustered(k_fsk_fwd<LOGM, R>, R, p.n_items * R, fsk_fft_threads<LOGM>(),
+                          fsk_fft_smem<LOGM, LOGN>(), p, s);
+}
+
+template <int LOGM, int R>
+cudaError_t corr_one(const FskCorrParams& p, cudaStream_t s) {
+  constexpr int LOGN = LOGM + ct_log2(R);
+  const int items = ((p.nw + 1) / 2) * p.Cg;
+  return launch_clustered(k_fsk_corr<LOGM, R>, R, items * R, fsk_fft_threads<LOGM>(), fsk_fft_smem<LOGM, LOGN>(),
+                          p, s);
+}
+
+}  // namespace
+
+cudaError_t fsk_prepare_fft() {
+  cudaError_t e;
+  if ((e = prepare_one<10, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_one<11, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_one<12, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_one<13, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_one<14, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_one<14, 2>()) != cudaSuccess) return e;
+  if ((e = prepare_one<14, 4>()) != cudaSuccess) return e;
+  return prepare_one<14, 8>();
+}
+
+cudaError_t launch_fsk_fwd(int logN, const FskFwdParams& p, cudaStream_t s) {
+  if (p.n_items <= 0) return cudaSuccess;
+  switch (logN) {
+    case 10: return fwd_one<10, 1>(p, s);
+    case 11: return fwd_one<11, 1>(p, s);
+    case 12: return fwd_one<12, 1>(p, s);
+    case 13: return fwd_one<13, 1>(p, s);
+    case 14: return fwd_one<14, 1>(p, s);
+    case 15: return fwd_one<14, 2>(p, s);
+    case 16: return fwd_one<14, 4>(p, s);
+    case 17: return fwd_one<14, 8>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fsk_corr(int logN, const FskCorrParams& p, cudaStream_t s) {
+  if (p.nw <= 0 || p.Cg <= 0) return cudaSuccess;
+  switch (logN) {
+    case 10: return corr_one<10, 1>(p, s);
+    case 11: return corr_one<11, 1>(p, s);
+    case 12: return corr_one<12, 1>(p, s);
+    case 13: return corr_one<13, 1>(p, s);
+    case 14: return corr_one<14, 1>(p, s);
+    case 15: return corr_one<14, 2>(p, s);
+    case 16: return corr_one<14, 4>(p, s);
+    case 17: return corr_one<14, 8>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace atlas

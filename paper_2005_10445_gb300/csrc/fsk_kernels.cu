@@ -1,0 +1,257 @@
+// fsk_kernels.cu -- the FSK front end's element-wise and per-detection kernels:
+//
+//   k_fsk_demod    Section 3 steps 1-5 over a range of the stream: int16 (I, Q)
+//                  to float, the LO mix with an exact fixed-point phase, both
+//                  composed filters H_BP H_1 and H_BP H_0 (Section 4.1) by
+//                  overlap-save with 4096-point transforms in shared memory
+//                  (one forward, two inverse per block of 4096 - T + 1
+//                  outputs), magnitudes, d and u
+//   k_fsk_replica  step 6: the continuous-phase FSK replica of each code
+//   k_fsk_stats_part / _final
+//                  step 8 per candidate: w_c, q, p_c and the three
+//                  correlation values around the peak as direct FP64 sums (in
+//                  32 slices of the support, summed in order), the parabolic
+//                  arrival time, the record appended to the caller's list
+//   k_fsk_advance  advances the caller's running count by the group's candidates
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "acq_common.cuh"
+#include "fsk_internal.h"
+
+namespace atlas {
+
+constexpr int kFskLogE = 4;  // 16 values per thread in the demodulation transforms
+constexpr int kFskDemodThreads = (1 << kFskLogB) >> kFskLogE;
+
+// padded work buffer, the block's spectrum, |f_1|, twiddle tables
+constexpr size_t fsk_demod_smem() {
+  return sizeof(float2) * (BlockFFT<kFskLogB, kFskLogE, -1>::SMEM_ELEMS + (1 << kFskLogB) + TwTables<kFskLogB>::N) +
+         sizeof(float) * (1 << kFskLogB);
+}
+
+__global__ void __launch_bounds__(kFskDemodThreads) k_fsk_demod(FskDemodParams p) {
+  using FWD = BlockFFT<kFskLogB, kFskLogE, -1>;
+  using INV = BlockFFT<kFskLogB, kFskLogE, +1>;
+  constexpr int B = 1 << kFskLogB;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* Xs = sm + FWD::SMEM_ELEMS;
+  float2* sm_tw = Xs + B;
+  float* A1 = reinterpret_cast<float*>(sm_tw + TwTables<kFskLogB>::N);
+  load_tables<kFskLogB>(sm_tw, p.tw);
+  const int T = p.T;
+  const int64_t per = B - (T - 1);
+  // blocks sit on a grid fixed in stream coordinates (block b holds outputs
+  // [b per, (b+1) per)), so every output is computed the same way whatever
+  // range is asked for
+  const int64_t first = (p.start >= 0 ? p.start / per : -((-p.start + per - 1) / per)) * per;
+  const int64_t end = p.start + p.count;
+  const int64_t n_blocks = (end - first + per - 1) / per;
+  const short2* iq = reinterpret_cast<const short2*>(p.iq);
+  for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+    __syncthreads();  // tables ready; the previous block is done with Xs and A1
+    // transform position n holds input sample i0 + n; outputs n >= T - 1 are
+    // the linear convolution at i0 + n (no wrap-around)
+    const int64_t i0 = first + blk * per - (T - 1);
+    auto load = [&](int n) -> float2 {
+      const int64_t i = i0 + n;
+      if (i < 0 || i >= p.S) return make_float2(0.f, 0.f);
+      float2 x;
+      if (iq) {
+        const short2 v = iq[i];
+        x = make_float2((float)v.x, (float)v.y);
+      } else {
+        x = p.xf[i];
+      }
+      if (p.lo_inc) x = cmul(x, expi_neg((uint64_t)i * p.lo_inc));
+      return x;
+    };
+    auto keep = [&](int k, float2 v) { Xs[k] = v; };
+    FWD::run(sm, sm_tw, load, keep);
+    __syncthreads();  // the block's spectrum is complete
+    auto load1 = [&](int k) { return cmul(Xs[k], p.G1[k]); };
+    // each output index is emitted by the same thread in both inverse
+    // transforms, so A1 needs no barrier between them
+    auto mag1 = [&](int n, float2 v) { A1[n] = sqrtf(fmaf(v.x, v.x, v.y * v.y)); };
+    INV::run(sm, sm_tw, load1, mag1);
+    auto load0 = [&](int k) { return cmul(Xs[k], p.G0[k]); };
+    auto out = [&](int n, float2 v) {
+      const int64_t i = i0 + n;
+      if (n < T - 1 || i < p.start || i >= end) return;
+      float dd = 0.f, uu = 0.f;
+      if (i >= 0 && i < p.S_out) {
+        const float a1 = A1[n];
+        const float a0 = sqrtf(fmaf(v.x, v.x, v.y * v.y));
+        const float s = a1 + a0;
+        uu = a1 - a0;
+        dd = s > 0.f ? uu / s : 0.f;
+      }
+      p.d[i - p.start] = dd;
+      if (p.u) p.u[i - p.start] = uu;
+    };
+    INV::run(sm, sm_tw, load0, out);
+  }
+}
+
+__global__ void k_fsk_replica(FskReplicaParams p, int L) {
+  const int c = blockIdx.y;
+  const int64_t off = p.chip_off[c];
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < L; n += gridDim.x * blockDim.x) {
+    const int ci = n / p.sps;
+    const int within = n - ci * p.sps;
+    const int64_t ones = p.ones_before[off + ci] * p.sps + (p.chips[off + ci] > 0 ? within : 0);
+    const uint64_t ph = (uint64_t)ones * p.inc1 + (uint64_t)(n - ones) * p.inc0;
+    p.r[(int64_t)c * L + n] = expi_neg(0ull - ph);  // exp(+j 2 pi phase)
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kFskStatsThreads = 256;
+
+// Stage 1: candidate b's five sums over slice s of n (n in [s*chunk, (s+1)*chunk)),
+// FP64 accumulation of exact FP32 products; persistent over (candidate, slice).
+__global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_part(FskStatsParams p) {
+  __shared__ double red[5][kFskStatsThreads / 32];
+  const int n_items = *p.n_cand * kFskStatsSlices;
+  const int chunk = (p.n_c + kFskStatsSlices - 1) / kFskStatsSlices;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int b = item / kFskStatsSlices, sl = item % kFskStatsSlices;
+    const atlas_detection cd = p.cand[b];
+    const int64_t a = (int64_t)cd.window * p.hop + cd.lag;
+    const float* dc = p.dc + (int64_t)cd.code * p.ld;
+    auto dv = [&](int64_t i) -> double {
+      const int64_t k = i - p.base;
+      return (k >= 0 && k < p.len) ? (double)p.d[k] : 0.0;
+    };
+    double cm = 0.0, c0 = 0.0, cp = 0.0, q = 0.0, pc = 0.0;
+    const int n1 = min(p.n_c, (sl + 1) * chunk);
+    for (int n = sl * chunk + threadIdx.x; n < n1; n += blockDim.x) {
+      const double g = dc[n];  // products of two FP32 values are exact in FP64
+      const double d0 = dv(a + n);
+      const int64_t k = a + n - p.base;
+      const double u0 = (k >= 0 && k < p.len) ? (double)p.u[k] : 0.0;
+      cm = fma(g, dv(a - 1 + n), cm);
+      c0 = fma(g, d0, c0);
+      cp = fma(g, dv(a + 1 + n), cp);
+      q = fma(d0, d0, q);
+      pc = fma(g, u0, pc);
+    }
+    cm = warp_sum(cm);
+    c0 = warp_sum(c0);
+    cp = warp_sum(cp);
+    q = warp_sum(q);
+    pc = warp_sum(pc);
+    __syncthreads();  // the previous item's reduction has been read
+    if (lane == 0) {
+      red[0][warp] = cm;
+      red[1][warp] = c0;
+      red[2][warp] = cp;
+      red[3][warp] = q;
+      red[4][warp] = pc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+      double v = 0.0;
+      for (int w = 0; w < kFskStatsThreads / 32; ++w) v += red[threadIdx.x][w];
+      p.part[((int64_t)b * kFskStatsSlices + sl) * 5 + threadIdx.x] = v;
+    }
+  }
+}
+
+// Stage 2: per candidate, the slices summed in order (deterministic), the
+// parabolic arrival time, the record appended to the caller's list.
+__global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_final(FskStatsParams p) {
+  const int nc = *p.n_cand;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nc; b += gridDim.x * blockDim.x) {
+    const atlas_detection cd = p.cand[b];
+    const int64_t a = (int64_t)cd.window * p.hop + cd.lag;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int sl = 0; sl < kFskStatsSlices; ++sl)
+      for (int k = 0; k < 5; ++k) v[k] += p.part[((int64_t)b * kFskStatsSlices + sl) * 5 + k];
+    const double cm = v[0], c0 = v[1], cp = v[2];
+    double delta = 0.0;
+    if (a - 1 >= 0 && a + 1 <= p.S - p.n_c) {
+      const double pm = cm * cm, p0 = c0 * c0, pp = cp * cp;
+      const double den = pm - 2.0 * p0 + pp;
+      if (den < 0.0) {
+        delta = 0.5 * (pm - pp) / den;
+        delta = delta > 0.5 ? 0.5 : (delta < -0.5 ? -0.5 : delta);
+      }
+    }
+    const int idx = *p.count + b;
+    if (idx < p.capacity) {
+      atlas_fsk_detection o;
+      o.code = cd.code;
+      o.window = cd.window;
+      o.lag = cd.lag;
+      o.score = cd.score;
+      o.toa = (double)a + delta;
+      o.w_c = c0;
+      o.q = v[3];
+      o.p_c = v[4];
+      p.out[idx] = o;
+    }
+  }
+}
+
+__global__ void k_fsk_advance(int* count, const int* n) { *count += *n; }
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+int64_t fsk_demod_outputs_per_block(int T) { return (int64_t)(1 << kFskLogB) - (T - 1); }
+
+cudaError_t fsk_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_fsk_demod, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fsk_demod_smem());
+  if (e != cudaSuccess) return e;
+  return fsk_prepare_fft();
+}
+
+cudaError_t launch_fsk_demod(const FskDemodParams& p, cudaStream_t s) {
+  if (p.count <= 0) return cudaSuccess;
+  if (p.T < 1 || p.T > kFskMaxTaps) return cudaErrorInvalidValue;
+  const int64_t per = fsk_demod_outputs_per_block(p.T);
+  const int64_t blocks = (p.count + per - 1) / per + 1;  // the grid of blocks may straddle one more
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsk_demod, kFskDemodThreads, fsk_demod_smem());
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int grid = (int)(blocks < resident ? blocks : resident);
+  k_fsk_demod<<<grid, kFskDemodThreads, fsk_demod_smem(), s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fsk_replica(const FskReplicaParams& p, int n_codes, int L, cudaStream_t s) {
+  if (n_codes <= 0 || L <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((L + 255) / 256 < 1024 ? (L + 255) / 256 : 1024), (unsigned)n_codes);
+  k_fsk_replica<<<grid, 256, 0, s>>>(p, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fsk_stats(const FskStatsParams& p, int max_cand, cudaStream_t s) {
+  if (max_cand > 0) {
+    const int items = max_cand * kFskStatsSlices;
+    k_fsk_stats_part<<<items < 1216 ? items : 1216, kFskStatsThreads, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fsk_stats_final<<<(max_cand + kFskStatsThreads - 1) / kFskStatsThreads, kFskStatsThreads, 0, s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_fsk_advance<<<1, 1, 0, s>>>(p.count, p.n_cand);
+  return cudaGetLastError();
+}
+
+}  // namespace atlas

@@ -96,3 +96,89 @@ def test_null_context_calls(lib):
     assert lib.atlas_acq_run(None, None, None, 0, None, 0, None) == binding.ATLAS_ERR_INVALID_ARG
     assert lib.atlas_acq_windows(None, 0, 0, None, None, None) == binding.ATLAS_ERR_INVALID_ARG
     lib.atlas_acq_destroy(None)
+
+
+# --- FSK front end (include/atlas_fsk.h) ------------------------------------
+
+def fsk_header_functions():
+    src = open(os.path.join(ROOT, "include", "atlas_fsk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(atlas_[a-z_]+)\s*\(", src)))
+
+
+def test_fsk_header_lists_expected_functions():
+    assert fsk_header_functions() == sorted(binding.EXPORTED_FSK)
+
+
+def test_fsk_every_declared_symbol_is_exported(lib):
+    for name in fsk_header_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_fsk_struct_sizes_and_defaults(lib):
+    assert ctypes.sizeof(binding.FskDetection) == 48
+    assert ctypes.sizeof(binding.FskOpts) == 32
+    o = binding.FskOpts()
+    lib.atlas_fsk_default_opts(ctypes.byref(o))
+    assert o.threshold == 49.0 and o.fft_len == 0 and o.windows_per_launch == 0
+
+
+def _fsk_create(lib, chips, cpc, n_codes, sps, fs, taps, n_bp, opts=None, f1=5e5, f0=-5e5, f_lo=0.0):
+    ctx = ctypes.c_void_p()
+    chips = np.ascontiguousarray(chips, np.int8)
+    cpc = np.ascontiguousarray(cpc, np.int32)
+    taps = np.ascontiguousarray(taps, np.float64)
+    st = lib.atlas_fsk_create(ctypes.byref(ctx), chips.ctypes.data, cpc.ctypes.data, n_codes, sps, fs, f1, f0,
+                              f_lo, taps.ctypes.data, n_bp, ctypes.byref(opts) if opts is not None else None)
+    assert not ctx.value
+    return st
+
+
+def test_fsk_create_rejects_bad_arguments(lib):
+    ch = np.ones(1000, np.int8)
+    taps = np.zeros((200, 2))
+    taps[:, 0] = 1.0 / 200
+    E = binding.ATLAS_ERR_INVALID_ARG
+    assert _fsk_create(lib, ch, [1000], 0, 2, 2e6, taps, 200) == E         # no codes
+    assert _fsk_create(lib, ch, [1000], 1, 0, 2e6, taps, 200) == E         # sps 0
+    assert _fsk_create(lib, ch, [1000], 1, 2, 0.0, taps, 200) == E         # fs 0
+    assert _fsk_create(lib, ch, [1000], 1, 2, 2e6, taps, 0) == E           # no taps
+    assert _fsk_create(lib, ch, [0], 1, 2, 2e6, taps, 200) == E            # empty code
+    assert _fsk_create(lib, ch, [1000], 1, 2, 2e6, taps, 200, f1=float("nan")) == E
+    bad_taps = taps.copy()
+    bad_taps[3, 1] = float("inf")
+    assert _fsk_create(lib, ch, [1000], 1, 2, 2e6, bad_taps, 200) == E
+    bad = ch.copy()
+    bad[7] = 0
+    assert _fsk_create(lib, bad, [1000], 1, 2, 2e6, taps, 200) == E        # chip not +/-1
+    o = binding.FskOpts()
+    lib.atlas_fsk_default_opts(ctypes.byref(o))
+    o.threshold = -2.0
+    assert _fsk_create(lib, ch, [1000], 1, 2, 2e6, taps, 200, o) == E
+
+
+def test_fsk_create_rejects_unsupported_sizes(lib):
+    U = binding.ATLAS_ERR_UNSUPPORTED
+    ch = np.ones(20000, np.int8)
+    taps = np.zeros((1100, 2))
+    taps[:, 0] = 1e-3
+    assert _fsk_create(lib, ch[:1000], [1000], 1, 2, 2e6, taps, 1100) == U     # T = 1101 taps > 1024
+    assert _fsk_create(lib, ch, [20000], 1, 8, 8e6, taps, 200) == U            # N = 2^19 > 2^17
+    o = binding.FskOpts()
+    lib.atlas_fsk_default_opts(ctypes.byref(o))
+    o.fft_len = 5000                                                          # not a power of two
+    assert _fsk_create(lib, ch[:1000], [1000], 1, 2, 2e6, taps, 200, o) == U
+    o.fft_len = 512                                                           # below 2^10
+    assert _fsk_create(lib, ch[:100], [100], 1, 2, 2e6, taps, 20, o) == U
+    o.fft_len = 2048                                                          # N <= n_c = 2000 + 200
+    assert _fsk_create(lib, ch[:1000], [1000], 1, 2, 2e6, taps, 200, o) == U
+
+
+def test_fsk_null_context_calls(lib):
+    E = binding.ATLAS_ERR_INVALID_ARG
+    assert lib.atlas_fsk_run(None, None, None, 0, None, 0, None) == E
+    assert lib.atlas_fsk_windows(None, 0, 1, None, None, None, None) == E
+    assert lib.atlas_fsk_demod(None, None, None, 0, 0, 0, None, None) == E
+    assert lib.atlas_fsk_code_demod(None, 0, None, 0, None) == E
+    lib.atlas_fsk_destroy(None)
