@@ -496,7 +496,7 @@ def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
     demod_tf = demod_samples * fsk_demod_flops_per_sample(T) / (demod_avg / 1e3) / 1e12
     corr_share = prof["corr_ms"] / total_ms
     demod_share = prof["demod_ms"] / total_ms
-    dom = ("k_fsk_corr (packed inverse N-point transform over a cluster of 8 blocks, corr^2, floor, argmax per "
+    dom = ("k_fsk_corr (packed inverse N-point transform over a cluster of 16 blocks, corr^2, floor, argmax per "
            "(window pair, code))", corr_units, fsk_corr_flops_per_cell(N), corr_avg, corr_tf, corr_share) \
         if corr_share >= demod_share else \
         ("k_fsk_demod (int16 conversion, LO mix, both composed filters by 4096-point overlap-save transforms, d, u)",

@@ -199,7 +199,7 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
       g.N = o.fft_len ? o.fft_len : 2 * (int)(1ll << ilog2_ceil(g.L));
       g.logN = ilog2_ceil(g.N);
       if (g.logN < atlas::kFskMinLogN || g.logN > atlas::kFskMaxLogN || g.N <= g.n_c) return ATLAS_ERR_UNSUPPORTED;
-      g.R = g.logN > atlas::kFskLogMBlock ? 1 << (g.logN - atlas::kFskLogMBlock) : 1;
+      g.R = g.logN > atlas::kFskLogMBlock ? 1 << (g.logN - atlas::kFskLogMCluster) : 1;
       g.hop = g.N - g.n_c;
       by_len[nch] = (int)ctx->groups.size();
       ctx->groups.push_back(g);
@@ -214,7 +214,6 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
 
   CK(cudaGetDevice(&ctx->device));
   CK(atlas::fsk_prepare());
-  CK(atlas::prepare_kernels());  // k_select
 
   // composed filters and their 4096-point spectra (FP64 on the host)
   std::vector<cd> h(n_bp);
@@ -441,7 +440,7 @@ int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S
       sp.capacity = nw * Cg;
       sp.count = ctx->d_ncand;
       sp.cells = nullptr;
-      CK(atlas::launch_select(sp, st));
+      CK(atlas::launch_fsk_select(sp, st));
       atlas::FskStatsParams tp;
       tp.cand = ctx->d_cand;
       tp.n_cand = ctx->d_ncand;

@@ -1,8 +1,10 @@
 // fsk_fft.cu -- the N-point transforms of the FSK cross-correlation (Section 3
-// step 7, computed with FFTs as in Section 4.1).  N = R * M: M <= 2^14 points
-// live in one block's shared memory and R in {1, 2, 4, 8} blocks of a
-// thread-block cluster exchange through distributed shared memory, so a
-// transform of up to 2^17 points never goes through global memory.
+// step 7, computed with FFTs as in Section 4.1).  N = R * M: M points live in
+// one block's shared memory (all of N up to 2^14 in one block; 2^13 per block
+// beyond) and R in {4, 8, 16} blocks of a thread-block cluster exchange through
+// distributed shared memory, so a transform of up to 2^17 points never goes
+// through global memory.  With 2^13 points (75 KB) per block three blocks fit
+// on an SM, and clusters of up to 16 blocks spread over every SM.
 //
 // Index maps (n = m + M n2, k = R k2 + r with m, k2 < M and n2, r < R):
 //   forward   X[R k2 + r] = sum_m W_M^{m k2} ( W_N^{m r} sum_n2 x[m + M n2] W_R^{n2 r} )
@@ -67,8 +69,12 @@ __device__ __forceinline__ float fsk_fwd_value(const FskFwdParams& p, int item, 
   return (i >= 0 && i < p.len) ? p.d[i] : 0.f;
 }
 
+// blocks per SM the cluster kernels are compiled for (register budget)
+template <int R>
+constexpr int fsk_min_blocks() { return R > 1 ? 3 : 1; }
+
 template <int LOGM, int R>
-__global__ void __launch_bounds__(fsk_fft_threads<LOGM>()) k_fsk_fwd(FskFwdParams p) {
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) k_fsk_fwd(FskFwdParams p) {
   using FFT = BlockFFT<LOGM, kLogE, -1>;
   constexpr int M = 1 << LOGM;
   constexpr int N = M * R;
@@ -120,7 +126,7 @@ __device__ __forceinline__ int fsk_valid_lags(const FskCorrParams& p, int w) {
 }
 
 template <int LOGM, int R>
-__global__ void __launch_bounds__(fsk_fft_threads<LOGM>()) k_fsk_corr(FskCorrParams p) {
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) k_fsk_corr(FskCorrParams p) {
   using FFT = BlockFFT<LOGM, kLogE, +1>;
   constexpr int M = 1 << LOGM;
   constexpr int N = M * R;
@@ -197,8 +203,16 @@ cudaError_t prepare_one() {
   cudaError_t e = cudaFuncSetAttribute(k_fsk_fwd<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fsk_fft_smem<LOGM, LOGN>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)fsk_fft_smem<LOGM, LOGN>());
+  if ((e = cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fsk_fft_smem<LOGM, LOGN>())) != cudaSuccess)
+    return e;
+  if constexpr (R > 8) {  // clusters of 16 blocks are beyond the portable size
+    if ((e = cudaFuncSetAttribute(k_fsk_fwd<LOGM, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+        cudaSuccess)
+      return e;
+    return cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  return cudaSuccess;
 }
 
 template <class P>
@@ -243,9 +257,9 @@ cudaError_t fsk_prepare_fft() {
   if ((e = prepare_one<12, 1>()) != cudaSuccess) return e;
   if ((e = prepare_one<13, 1>()) != cudaSuccess) return e;
   if ((e = prepare_one<14, 1>()) != cudaSuccess) return e;
-  if ((e = prepare_one<14, 2>()) != cudaSuccess) return e;
-  if ((e = prepare_one<14, 4>()) != cudaSuccess) return e;
-  return prepare_one<14, 8>();
+  if ((e = prepare_one<13, 4>()) != cudaSuccess) return e;
+  if ((e = prepare_one<13, 8>()) != cudaSuccess) return e;
+  return prepare_one<13, 16>();
 }
 
 cudaError_t launch_fsk_fwd(int logN, const FskFwdParams& p, cudaStream_t s) {
@@ -256,9 +270,9 @@ cudaError_t launch_fsk_fwd(int logN, const FskFwdParams& p, cudaStream_t s) {
     case 12: return fwd_one<12, 1>(p, s);
     case 13: return fwd_one<13, 1>(p, s);
     case 14: return fwd_one<14, 1>(p, s);
-    case 15: return fwd_one<14, 2>(p, s);
-    case 16: return fwd_one<14, 4>(p, s);
-    case 17: return fwd_one<14, 8>(p, s);
+    case 15: return fwd_one<13, 4>(p, s);
+    case 16: return fwd_one<13, 8>(p, s);
+    case 17: return fwd_one<13, 16>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -271,9 +285,9 @@ cudaError_t launch_fsk_corr(int logN, const FskCorrParams& p, cudaStream_t s) {
     case 12: return corr_one<12, 1>(p, s);
     case 13: return corr_one<13, 1>(p, s);
     case 14: return corr_one<14, 1>(p, s);
-    case 15: return corr_one<14, 2>(p, s);
-    case 16: return corr_one<14, 4>(p, s);
-    case 17: return corr_one<14, 8>(p, s);
+    case 15: return corr_one<13, 4>(p, s);
+    case 16: return corr_one<13, 8>(p, s);
+    case 17: return corr_one<13, 16>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }

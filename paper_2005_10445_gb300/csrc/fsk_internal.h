@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "acq_internal.h"
 #include "atlas_acq.h"
 #include "atlas_fsk.h"
 
@@ -15,7 +16,8 @@ constexpr int kFskLogB = 12;          // demodulation block: 4096-point transfor
 constexpr int kFskMaxTaps = 1024;     // composed filter taps T (<= B / 4)
 constexpr int kFskMinLogN = 10;
 constexpr int kFskMaxLogN = 17;
-constexpr int kFskLogMBlock = 14;     // largest transform one block holds; larger N span a cluster
+constexpr int kFskLogMBlock = 14;     // largest transform one block holds alone
+constexpr int kFskLogMCluster = 13;   // points per block when a transform spans a cluster
 constexpr int kFskStatsSlices = 32;   // slices of the support per candidate in the peak sums
 
 // Steps 1-5 over an index range of the stream (or of a replica): conversion,
@@ -104,6 +106,8 @@ cudaError_t launch_fsk_replica(const FskReplicaParams& p, int n_codes, int L, cu
 // logN in [kFskMinLogN, kFskMaxLogN]
 cudaError_t launch_fsk_fwd(int logN, const FskFwdParams& p, cudaStream_t s);
 cudaError_t launch_fsk_corr(int logN, const FskCorrParams& p, cudaStream_t s);
+// selection of a launch group (SelectParams with K = 1, sps = R partials per cell)
+cudaError_t launch_fsk_select(const SelectParams& p, cudaStream_t s);
 cudaError_t launch_fsk_stats(const FskStatsParams& p, int max_cand, cudaStream_t s);
 
 }  // namespace atlas

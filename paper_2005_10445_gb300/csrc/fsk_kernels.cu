@@ -12,6 +12,8 @@
 //                  correlation values around the peak as direct FP64 sums (in
 //                  32 slices of the support, summed in order), the parabolic
 //                  arrival time, the record appended to the caller's list
+//   k_fsk_select   per (window, code): combines the cluster's partial results,
+//                  score, threshold, ordered compaction by a block prefix sum
 //   k_fsk_advance  advances the caller's running count by the group's candidates
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -203,6 +205,71 @@ __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_final(FskStatsPa
 
 __global__ void k_fsk_advance(int* count, const int* n) { *count += *n; }
 
+// Selection of a launch group (Section 3 step 8): per (window, code) the
+// R partial results of the cluster's blocks are combined (floor = sum / N,
+// the maximum with the smallest lag on ties), score = P* / floor, and the
+// cells at or above the threshold are appended in (window, code) order by
+// a block-wide prefix sum, kFskSelectThreads cells per round.
+constexpr int kFskSelectThreads = 1024;
+
+__global__ void __launch_bounds__(kFskSelectThreads) k_fsk_select(SelectParams p) {
+  __shared__ int warp_tot[kFskSelectThreads / 32];
+  __shared__ int base_sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base_sh = *p.count;
+  const int n_pairs = p.nw * p.Cg;
+  for (int p0 = 0; p0 < n_pairs; p0 += kFskSelectThreads) {
+    const int pi = p0 + threadIdx.x;
+    int flag = 0;
+    atlas_detection d;
+    if (pi < n_pairs) {
+      const float4* pr = p.part + (int64_t)pi * p.sps;
+      float sum = 0.f, best = -1.f;
+      int bt = 0x7fffffff;
+      for (int r = 0; r < p.sps; ++r) {
+        const float4 v = pr[r];
+        sum += v.x;
+        better(best, bt, v.y, __float_as_int(v.z));
+      }
+      const float floor_ = sum / (float)p.N;
+      const float score = floor_ > 0.f ? best / floor_ : 0.f;
+      flag = score >= p.threshold ? 1 : 0;
+      d.code = p.codes[pi % p.Cg];
+      d.window = p.w0 + pi / p.Cg;
+      d.lag = bt;
+      d.freq_bin = 0;
+      d.score = score;
+      d.peak_power = best;
+      d.toa = 0.0;
+    }
+    // exclusive prefix sum of the flags over the block
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    const int in_warp = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    if (warp == 0) {
+      const int v = warp_tot[lane];
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      warp_tot[lane] = x - v;  // exclusive
+    }
+    __syncthreads();
+    const int base = base_sh;
+    if (flag) {
+      const int idx = base + warp_tot[warp] + in_warp;
+      if (idx < p.capacity) p.out[idx] = d;
+    }
+    __syncthreads();  // every thread has read base_sh and warp_tot
+    if (threadIdx.x == kFskSelectThreads - 1) base_sh = base + warp_tot[warp] + in_warp + flag;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *p.count = base_sh;
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -238,6 +305,11 @@ cudaError_t launch_fsk_replica(const FskReplicaParams& p, int n_codes, int L, cu
   if (n_codes <= 0 || L <= 0) return cudaSuccess;
   dim3 grid((unsigned)((L + 255) / 256 < 1024 ? (L + 255) / 256 : 1024), (unsigned)n_codes);
   k_fsk_replica<<<grid, 256, 0, s>>>(p, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fsk_select(const SelectParams& p, cudaStream_t s) {
+  k_fsk_select<<<1, kFskSelectThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
