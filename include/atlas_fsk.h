@@ -103,6 +103,24 @@ int atlas_fsk_windows(atlas_fsk_t ctx, int32_t code, int64_t n_samples, int32_t*
 int atlas_fsk_run(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t n_samples,
                   atlas_fsk_detection* d_out, int32_t capacity, int32_t* d_count);
 
+/*
+ * The search restricted to a subset of the codes, on a block of a longer
+ * stream.
+ *   first_sample  absolute index of d_iq[0] in the receiver's stream: the LO
+ *                 phase of step 2 continues from it (windows, lags and ToAs
+ *                 stay relative to d_iq)
+ *   h_codes       host, n_sel distinct code indices (read before the call
+ *                 returns); NULL searches every code; n_sel = 0 with a
+ *                 non-NULL list searches nothing and writes *d_count = 0
+ *   n_samples     >= the largest support n_c of the listed codes
+ * Detections are ordered by (code length group, window, code).  Used for the
+ * tracking tasks (one code, a block around a predicted arrival) and for the
+ * searching queue of the scheduler (atlas_rt_*).
+ */
+int atlas_fsk_run_codes(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t n_samples,
+                        int64_t first_sample, const int32_t* h_codes, int32_t n_sel, atlas_fsk_detection* d_out,
+                        int32_t capacity, int32_t* d_count);
+
 /* The same with host buffers: copies h_iq in, searches, copies the records and
  * the count out, and synchronises.  Device staging buffers are allocated on
  * first use for a size and kept. */

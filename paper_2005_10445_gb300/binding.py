@@ -38,7 +38,8 @@ EXPORTED = [
 ]
 # Every symbol include/atlas_fsk.h declares.
 EXPORTED_FSK = [
-    "atlas_fsk_default_opts", "atlas_fsk_create", "atlas_fsk_windows", "atlas_fsk_run", "atlas_fsk_run_host",
+    "atlas_fsk_default_opts", "atlas_fsk_create", "atlas_fsk_windows", "atlas_fsk_run", "atlas_fsk_run_codes",
+    "atlas_fsk_run_host",
     "atlas_fsk_demod", "atlas_fsk_code_demod", "atlas_fsk_profile_begin", "atlas_fsk_profile_end",
     "atlas_fsk_last_error", "atlas_fsk_destroy",
 ]
@@ -182,6 +183,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_fsk_windows.restype = ctypes.c_int
     lib.atlas_fsk_run.argtypes = [vp, vp, vp, i64, vp, i32, vp]
     lib.atlas_fsk_run.restype = ctypes.c_int
+    lib.atlas_fsk_run_codes.argtypes = [vp, vp, vp, i64, i64, vp, i32, vp, i32, vp]
+    lib.atlas_fsk_run_codes.restype = ctypes.c_int
     lib.atlas_fsk_run_host.argtypes = [vp, vp, vp, i64, vp, i32, vp]
     lib.atlas_fsk_run_host.restype = ctypes.c_int
     lib.atlas_fsk_demod.argtypes = [vp, vp, vp, i64, i64, i64, vp, vp]
@@ -519,6 +522,19 @@ class FskSearch:
 
     def run_ptr(self, stream: int, d_iq: int, n_samples: int, d_out: int, capacity: int, d_count: int) -> None:
         _check_fsk(self._lib.atlas_fsk_run(self.ctx, stream, d_iq, n_samples, d_out, capacity, d_count), self.ctx)
+
+    def run_codes_ptr(self, stream: int, d_iq: int, n_samples: int, first_sample: int, codes, d_out: int,
+                      capacity: int, d_count: int) -> None:
+        """codes: None for every code, else a list of code indices (may be empty)."""
+        if codes is None:
+            ptr, n = None, 0
+        else:
+            lst = np.asarray(codes, np.int32).reshape(-1)
+            sel = np.zeros(max(lst.size, 1), np.int32)
+            sel[: lst.size] = lst
+            ptr, n = sel.ctypes.data, lst.size
+        _check_fsk(self._lib.atlas_fsk_run_codes(self.ctx, stream, d_iq, n_samples, first_sample, ptr, n, d_out,
+                                                 capacity, d_count), self.ctx)
 
     def run_host_ptr(self, stream: int, h_iq: int, n_samples: int, h_out: int, capacity: int,
                      h_count: int) -> None:

@@ -61,6 +61,12 @@ struct atlas_fsk_ctx {
   int cand_cap = 0;
   int* d_ncand = nullptr;
   double* d_stats_part = nullptr;
+  // code selection of atlas_fsk_run_codes: per group, the group-local indices
+  // then the global ids of the searched codes (pinned host staging, device copy)
+  int* h_sel = nullptr;
+  int* d_sel = nullptr;
+  cudaEvent_t ev_sel = nullptr;
+  bool sel_pending = false;
   // host-buffer path
   int16_t* d_stage = nullptr;
   int64_t stage_samples = 0;
@@ -114,6 +120,9 @@ void free_ctx(atlas_fsk_ctx* ctx) {
   cudaFree(ctx->d_cand);
   cudaFree(ctx->d_ncand);
   cudaFree(ctx->d_stats_part);
+  cudaFreeHost(ctx->h_sel);
+  cudaFree(ctx->d_sel);
+  if (ctx->ev_sel) cudaEventDestroy(ctx->ev_sel);
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_stage_out);
   cudaFree(ctx->d_stage_count);
@@ -351,16 +360,51 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
       cudaMalloc((void**)&ctx->d_stats_part, sizeof(double) * 5 * atlas::kFskStatsSlices * (size_t)cand) !=
           cudaSuccess)
     return ATLAS_ERR_NO_MEMORY;
+  if (cudaMallocHost((void**)&ctx->h_sel, sizeof(int) * 2 * (size_t)n_codes) != cudaSuccess ||
+      cudaMalloc((void**)&ctx->d_sel, sizeof(int) * 2 * (size_t)n_codes) != cudaSuccess)
+    return ATLAS_ERR_NO_MEMORY;
+  CK(cudaEventCreateWithFlags(&ctx->ev_sel, cudaEventDisableTiming));
   return ATLAS_OK;
 }
 
-int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S, atlas_fsk_detection* d_out,
-             int capacity, int* d_count) {
+// sel: host list of the searched codes (n_sel of them), or null for every code.
+int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S, int64_t first_sample,
+             const int32_t* sel, int n_sel, atlas_fsk_detection* d_out, int capacity, int* d_count) {
+  // per group: offset of its lists in h_sel / d_sel and its number of searched codes
+  std::vector<int> sel_off(ctx->groups.size(), 0), sel_n(ctx->groups.size(), 0);
+  if (sel) {
+    std::vector<char> on(ctx->C, 0);
+    for (int i = 0; i < n_sel; ++i) {
+      if (sel[i] < 0 || sel[i] >= ctx->C || on[sel[i]]) return ATLAS_ERR_INVALID_ARG;
+      on[sel[i]] = 1;
+    }
+    if (ctx->sel_pending) CK(cudaEventSynchronize(ctx->ev_sel));  // the previous list has been copied
+    int off = 0;
+    for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+      const FskGroup& g = ctx->groups[gi];
+      sel_off[gi] = off;
+      int n = 0;
+      for (size_t i = 0; i < g.codes.size(); ++i)
+        if (on[g.codes[i]]) ctx->h_sel[off + n++] = (int)i;  // ascending: (window, code) order is kept
+      for (int i = 0; i < n; ++i) ctx->h_sel[off + n + i] = g.codes[ctx->h_sel[off + i]];
+      sel_n[gi] = n;
+      off += 2 * n;
+    }
+    if (off > 0) {
+      CK(cudaMemcpyAsync(ctx->d_sel, ctx->h_sel, sizeof(int) * off, cudaMemcpyHostToDevice, st));
+      CK(cudaEventRecord(ctx->ev_sel, st));
+      ctx->sel_pending = true;
+    }
+  }
   CK(cudaMemsetAsync(d_count, 0, sizeof(int), st));
   const float2* twB = ctx->d_tw.at(atlas::kFskLogB);
-  for (const FskGroup& g : ctx->groups) {
+  for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+    const FskGroup& g = ctx->groups[gi];
     const int W = g.windows(S);
-    const int Cg = (int)g.codes.size();
+    const int Cg = sel ? sel_n[gi] : (int)g.codes.size();
+    if (Cg == 0) continue;
+    const int* d_sel_local = sel ? ctx->d_sel + sel_off[gi] : nullptr;
+    const int* d_sel_global = sel ? ctx->d_sel + sel_off[gi] + Cg : g.d_codes;
     for (int w0 = 0; w0 < W; w0 += ctx->wc) {
       const int nw = std::min(ctx->wc, W - w0);
       // demodulated range of the group's windows, one sample of margin on each
@@ -375,6 +419,7 @@ int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S
       dp.count = len;
       dp.T = ctx->T;
       dp.lo_inc = ctx->lo_inc;
+      dp.lo_first = first_sample;
       dp.G1 = ctx->d_G1;
       dp.G0 = ctx->d_G0;
       dp.tw = twB;
@@ -412,6 +457,7 @@ int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S
       cp.w0 = w0;
       cp.nw = nw;
       cp.Cg = Cg;
+      cp.sel = d_sel_local;
       const bool tc = ctx->profiling && 2 * ctx->corr_used + 1 < (int)ctx->ev_corr.size();
       if (tc) CK(cudaEventRecord(ctx->ev_corr[2 * ctx->corr_used], st));
       CK(atlas::launch_fsk_corr(g.logN, cp, st));
@@ -426,7 +472,7 @@ int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S
       CK(cudaMemsetAsync(ctx->d_ncand, 0, sizeof(int), st));
       atlas::SelectParams sp;
       sp.part = ctx->d_part;
-      sp.codes = g.d_codes;
+      sp.codes = d_sel_global;
       sp.Cg = Cg;
       sp.C = ctx->C;
       sp.K = 1;
@@ -512,15 +558,36 @@ int atlas_fsk_windows(atlas_fsk_t ctx, int32_t code, int64_t n_samples, int32_t*
   return ATLAS_OK;
 }
 
-int atlas_fsk_run(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t n_samples,
-                  atlas_fsk_detection* d_out, int32_t capacity, int32_t* d_count) {
+int atlas_fsk_run_codes(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t n_samples,
+                        int64_t first_sample, const int32_t* h_codes, int32_t n_sel, atlas_fsk_detection* d_out,
+                        int32_t capacity, int32_t* d_count) {
   if (!ctx || !d_iq || !d_count || capacity < 0 || (capacity > 0 && !d_out)) return ATLAS_ERR_INVALID_ARG;
-  if (n_samples < ctx->max_nc || n_samples > ((int64_t)1 << 40)) return ATLAS_ERR_INVALID_ARG;
+  if (n_sel < 0 || (n_sel > 0 && !h_codes) || first_sample < 0) return ATLAS_ERR_INVALID_ARG;
+  if (n_samples > ((int64_t)1 << 40) || first_sample > ((int64_t)1 << 62)) return ATLAS_ERR_INVALID_ARG;
+  int max_nc = 0;
+  if (h_codes) {
+    for (int i = 0; i < n_sel; ++i)
+      if (h_codes[i] >= 0 && h_codes[i] < ctx->C)
+        max_nc = std::max(max_nc, ctx->groups[ctx->code_group[h_codes[i]]].n_c);
+  } else {
+    max_nc = ctx->max_nc;
+  }
+  if (n_samples < max_nc) return ATLAS_ERR_INVALID_ARG;
   for (const FskGroup& g : ctx->groups)
     if ((int64_t)g.windows(n_samples) * g.hop + g.N > ((int64_t)1 << 31) - 2) return ATLAS_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device) return ATLAS_ERR_INVALID_ARG;
-  return run_impl(ctx, (cudaStream_t)stream, d_iq, n_samples, d_out, capacity, d_count);
+  if (h_codes && n_sel == 0) {  // nothing to search
+    CK(cudaMemsetAsync(d_count, 0, sizeof(int), (cudaStream_t)stream));
+    return ATLAS_OK;
+  }
+  return run_impl(ctx, (cudaStream_t)stream, d_iq, n_samples, first_sample, h_codes, n_sel, d_out, capacity,
+                  d_count);
+}
+
+int atlas_fsk_run(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t n_samples,
+                  atlas_fsk_detection* d_out, int32_t capacity, int32_t* d_count) {
+  return atlas_fsk_run_codes(ctx, stream, d_iq, n_samples, 0, nullptr, 0, d_out, capacity, d_count);
 }
 
 int atlas_fsk_run_host(atlas_fsk_t ctx, void* stream, const int16_t* h_iq, int64_t n_samples,

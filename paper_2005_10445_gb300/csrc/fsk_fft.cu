@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) 
   const int nv0 = fsk_valid_lags(p, p.w0 + wl0);
   const int nv1 = has1 ? fsk_valid_lags(p, p.w0 + wl1) : 0;
   const float2* X = p.X + (int64_t)pr * N + (int64_t)rank * M;
-  const float2* C = p.C + (int64_t)c * N + (int64_t)rank * M;
+  const float2* C = p.C + (int64_t)(p.sel ? p.sel[c] : c) * N + (int64_t)rank * M;
   auto load = [&](int k) { return cmul(X[k], C[k]); };
   float s0 = 0.f, b0 = -1.f, s1 = 0.f, b1 = -1.f;
   int t0 = INT_MAX, t1 = INT_MAX;

@@ -32,6 +32,7 @@ struct FskDemodParams {
   int64_t start, count;
   int T;                        // composed filter taps
   uint64_t lo_inc;              // LO phase per sample, turns * 2^64 (x * exp(-j 2 pi f_lo i / fs))
+  int64_t lo_first = 0;         // absolute stream index of input sample 0 (the LO phase continues across calls)
   const float2* G1;             // [B] FFT_B(g_1 zero padded) / B
   const float2* G0;             // [B]
   const float2* tw;             // twiddle tables of B
@@ -79,6 +80,7 @@ struct FskCorrParams {
   int64_t S;
   int N, hop, W, n_c;
   int w0, nw, Cg;
+  const int* sel = nullptr;     // optional [Cg] group-local indices of the searched codes
 };
 
 // Per candidate of a launch group: the direct FP64 sums at the peak and the

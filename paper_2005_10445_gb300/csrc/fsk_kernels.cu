@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kFskDemodThreads) k_fsk_demod(FskDemodParams p
       } else {
         x = p.xf[i];
       }
-      if (p.lo_inc) x = cmul(x, expi_neg((uint64_t)i * p.lo_inc));
+      if (p.lo_inc) x = cmul(x, expi_neg((uint64_t)(i + p.lo_first) * p.lo_inc));
       return x;
     };
     auto keep = [&](int k, float2 v) { Xs[k] = v; };
