@@ -36,6 +36,11 @@ EXPORTED = [
     "atlas_prop_features", "atlas_prop_loss_grad", "atlas_prop_adam", "atlas_prop_logits", "atlas_prop_candidates",
     "atlas_acq_run_proposed", "atlas_prop_last_error", "atlas_prop_destroy",
 ]
+# Every symbol include/atlas_rt.h declares.
+EXPORTED_RT = [
+    "atlas_rt_default_opts", "atlas_rt_create", "atlas_rt_push", "atlas_rt_pump", "atlas_rt_get_stats",
+    "atlas_rt_last_error", "atlas_rt_destroy",
+]
 # Every symbol include/atlas_fsk.h declares.
 EXPORTED_FSK = [
     "atlas_fsk_default_opts", "atlas_fsk_create", "atlas_fsk_windows", "atlas_fsk_run", "atlas_fsk_run_codes",
@@ -83,6 +88,25 @@ class FskProfile(ctypes.Structure):
                 ("corr_timed", ctypes.c_int64), ("corr_ms", ctypes.c_double), ("demod_launches", ctypes.c_int64),
                 ("demod_samples", ctypes.c_int64), ("demod_timed", ctypes.c_int64), ("demod_ms", ctypes.c_double)]
 
+
+class RtOpts(ctypes.Structure):
+    _fields_ = [("ring_samples", ctypes.c_int64), ("search_block", ctypes.c_int32),
+                ("search_overlap", ctypes.c_int32), ("track_block", ctypes.c_int32), ("max_misses", ctypes.c_int32),
+                ("capacity", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class RtStats(ctypes.Structure):
+    _fields_ = [("pushed", ctypes.c_int64), ("search_tasks", ctypes.c_int64), ("track_tasks", ctypes.c_int64),
+                ("searched_samples", ctypes.c_int64), ("search_units", ctypes.c_int64),
+                ("track_units", ctypes.c_int64), ("events", ctypes.c_int64), ("search_ms", ctypes.c_double),
+                ("track_ms", ctypes.c_double), ("searching", ctypes.c_int32), ("tracking", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+RT_SEARCH_DETECTION, RT_TRACK_DETECTION, RT_TRACK_MISS, RT_TRACK_LOST, RT_SEARCH_SKIPPED = range(5)
+RT_EVENT_DTYPE = np.dtype([("kind", "<i4"), ("code", "<i4"), ("task_start", "<i8"), ("toa", "<f8"),
+                           ("score", "<f4"), ("misses", "<i4"), ("w_c", "<f8"), ("q", "<f8")])
+assert RT_EVENT_DTYPE.itemsize == 48
 
 FSK_DETECTION_DTYPE = np.dtype([("code", "<i4"), ("window", "<i4"), ("lag", "<i4"), ("score", "<f4"),
                                 ("toa", "<f8"), ("w_c", "<f8"), ("q", "<f8"), ("p_c", "<f8")])
@@ -199,6 +223,20 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_fsk_last_error.restype = ctypes.c_char_p
     lib.atlas_fsk_destroy.argtypes = [vp]
     lib.atlas_fsk_destroy.restype = None
+    lib.atlas_rt_default_opts.argtypes = [ctypes.POINTER(RtOpts), f64]
+    lib.atlas_rt_default_opts.restype = None
+    lib.atlas_rt_create.argtypes = [ctypes.POINTER(vp), vp, vp, i32, ctypes.POINTER(RtOpts)]
+    lib.atlas_rt_create.restype = ctypes.c_int
+    lib.atlas_rt_push.argtypes = [vp, vp, vp, i64]
+    lib.atlas_rt_push.restype = ctypes.c_int
+    lib.atlas_rt_pump.argtypes = [vp, vp, i32, vp, i32, ctypes.POINTER(i32)]
+    lib.atlas_rt_pump.restype = ctypes.c_int
+    lib.atlas_rt_get_stats.argtypes = [vp, ctypes.POINTER(RtStats)]
+    lib.atlas_rt_get_stats.restype = ctypes.c_int
+    lib.atlas_rt_last_error.argtypes = [vp]
+    lib.atlas_rt_last_error.restype = ctypes.c_char_p
+    lib.atlas_rt_destroy.argtypes = [vp]
+    lib.atlas_rt_destroy.restype = None
     lib.atlas_acq_strerror.argtypes = [ctypes.c_int]
     lib.atlas_acq_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -584,3 +622,63 @@ class FskSearch:
         cnt = ctypes.c_int32()
         self.run_host_ptr(stream, a.ctypes.data, a.shape[0], out.ctypes.data, capacity, ctypes.addressof(cnt))
         return out[: min(cnt.value, capacity)].copy(), cnt.value
+
+
+# ---------------------------------------------------------------------------
+# continuous ingest and scheduler (include/atlas_rt.h)
+# ---------------------------------------------------------------------------
+
+def rt_default_opts(fs_hz: float) -> RtOpts:
+    o = RtOpts()
+    load().atlas_rt_default_opts(ctypes.byref(o), float(fs_hz))
+    return o
+
+
+class Runtime:
+    """Cyclic device buffer + searching/tracking scheduler over an FskSearch."""
+
+    def __init__(self, fsk: FskSearch, period_samples: Sequence[float], opts: Optional[RtOpts] = None,
+                 fs_hz: float = 8e6):
+        lib = load()
+        self._lib = lib
+        self.fsk = fsk  # kept alive: the runtime borrows the context
+        self.ctx = ctypes.c_void_p()
+        per = np.ascontiguousarray(np.asarray(period_samples, np.float64))
+        o = opts if opts is not None else rt_default_opts(fs_hz)
+        st = lib.atlas_rt_create(ctypes.byref(self.ctx), fsk.ctx, per.ctypes.data, per.size, ctypes.byref(o))
+        if st != ATLAS_OK:
+            self.ctx = None
+        _check(st)
+
+    def _chk(self, st):
+        if st != ATLAS_OK:
+            msg = strerror(st)
+            if st == ATLAS_ERR_CUDA:
+                msg += ": " + self._lib.atlas_rt_last_error(self.ctx).decode()
+            raise AtlasError(st, msg)
+
+    def push(self, iq16: np.ndarray, stream: int = 0) -> None:
+        a = np.ascontiguousarray(iq16, dtype=np.int16)
+        self._chk(self._lib.atlas_rt_push(self.ctx, stream, a.ctypes.data, a.shape[0]))
+
+    def pump(self, max_tasks: int = 0, cap: int = 4096, stream: int = 0) -> np.ndarray:
+        ev = np.zeros(max(cap, 1), RT_EVENT_DTYPE)
+        n = ctypes.c_int32()
+        self._chk(self._lib.atlas_rt_pump(self.ctx, stream, max_tasks, ev.ctypes.data, cap, ctypes.byref(n)))
+        return ev[: min(n.value, cap)].copy()
+
+    def stats(self) -> dict:
+        s = RtStats()
+        self._chk(self._lib.atlas_rt_get_stats(self.ctx, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in RtStats._fields_ if f != "reserved"}
+
+    def close(self) -> None:
+        if self.ctx:
+            self._lib.atlas_rt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

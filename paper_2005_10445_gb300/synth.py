@@ -474,3 +474,36 @@ def fsk_realistic(seed: int = 2, seconds: float = 1.0, n_codes: int = 16, n_chip
     chips = [random_chips(n, seed * 1_000_003 + c) for c, n in enumerate(lens)]
     return fsk_stream(seed, S, chips, sps, fs_hz, 5e5, -5e5, f_lo_hz, n_tags, snr_range,
                       name=f"fsk realistic: {S} samples at {fs_hz/1e6:g} MS/s, {len(chips)} codes, sps {sps}")
+
+
+def fsk_periodic(seed: int = 7, seconds: float = 1.0, fs_hz: float = 4e6, n_codes: int = 4, n_chips: int = 1024,
+                 sps: int = 4, period_s=(0.04, 0.06), snr_range=(-5.0, -2.0), f_lo_hz: float = 250e3,
+                 offset_hz: float = 2e3, sigma: float = 2048.0):
+    """A stream for the scheduler: every tag transmits its code periodically
+    (Section 2.2: tracked tags are predicted one period ahead).  Tag c's period
+    is drawn from period_s (seconds, rounded to whole samples) and its first
+    transmission from [0, period); each transmission has its own phase, a
+    carrier offset within +/-offset_hz and an SNR from snr_range.  Returns
+    (FskWorkload, periods in samples)."""
+    rng = np.random.default_rng(seed)
+    S = int(round(seconds * fs_hz))
+    chips = [random_chips(n_chips, seed * 1_000_003 + c) for c in range(n_codes)]
+    w = FskWorkload(f"fsk periodic: {S} samples at {fs_hz/1e6:g} MS/s, {n_codes} codes x {n_chips} chips, sps {sps}",
+                    np.zeros((0, 2), np.int16), chips, sps, fs_hz, 5e5, -5e5, f_lo_hz,
+                    bandpass_taps(200, 7.5e5, fs_hz), 0, [], sigma)
+    z = rng.standard_normal(2 * S) * sigma
+    x = z[0::2] + 1j * z[1::2]
+    L = n_chips * sps
+    periods = []
+    for c in range(n_codes):
+        per = int(round(rng.uniform(*period_s) * fs_hz))
+        periods.append(float(per))
+        d = int(rng.integers(0, per))
+        while d + L <= S:
+            tg = Tag(code=c, delay=float(d), freq_hz=float(rng.uniform(-offset_hz, offset_hz)), bin=-1,
+                     snr_db=float(rng.uniform(*snr_range)), phase=float(rng.uniform(0, 2 * math.pi)))
+            inject_fsk(x, w, tg)
+            w.tags.append(tg)
+            d += per
+    w.iq16 = quantise_iq(x)
+    return w, periods

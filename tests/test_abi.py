@@ -182,3 +182,40 @@ def test_fsk_null_context_calls(lib):
     assert lib.atlas_fsk_demod(None, None, None, 0, 0, 0, None, None) == E
     assert lib.atlas_fsk_code_demod(None, 0, None, 0, None) == E
     lib.atlas_fsk_destroy(None)
+
+
+# --- runtime (include/atlas_rt.h) -------------------------------------------
+
+def rt_header_functions():
+    src = open(os.path.join(ROOT, "include", "atlas_rt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(atlas_[a-z_]+)\s*\(", src)))
+
+
+def test_rt_header_and_exports(lib):
+    assert rt_header_functions() == sorted(binding.EXPORTED_RT)
+    for name in rt_header_functions():
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_rt_structs_and_defaults(lib):
+    assert ctypes.sizeof(binding.RtOpts) == 40
+    assert ctypes.sizeof(binding.RtStats) == 88
+    assert binding.RT_EVENT_DTYPE.itemsize == 48
+    o = binding.rt_default_opts(8e6)
+    assert (o.ring_samples, o.search_block, o.search_overlap, o.track_block, o.max_misses, o.capacity) == \
+        (128000000, 800000, 80000, 96000, 3, 1024)
+
+
+def test_rt_rejects_bad_arguments(lib):
+    E = binding.ATLAS_ERR_INVALID_ARG
+    o = binding.rt_default_opts(8e6)
+    per = np.ones(2)
+    ctx = ctypes.c_void_p()
+    assert lib.atlas_rt_create(ctypes.byref(ctx), None, per.ctypes.data, 2, ctypes.byref(o)) == E
+    assert not ctx.value
+    assert lib.atlas_rt_push(None, None, None, 0) == E
+    n = ctypes.c_int32()
+    assert lib.atlas_rt_pump(None, None, 0, None, 0, ctypes.byref(n)) == E
+    assert lib.atlas_rt_get_stats(None, None) == E
+    lib.atlas_rt_destroy(None)

@@ -1,0 +1,121 @@
+"""Continuous ingest and the scheduler (Section 2.2) on the GPU: periodic tags
+are first found by a searching task and then tracked at every transmission;
+the events agree with the FP64 FSK oracle run on the same task blocks; the
+task sequence is deterministic; buffer overruns are reported (GPU only)."""
+import numpy as np
+import pytest
+
+from oracle import fsk
+from paper_2005_10445_gb300 import synth
+
+from test_gpu_fsk import SCORE_RTOL, SUM_RTOL, TOA_ATOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(built_lib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def make_rt(w, periods, **opt):
+    from paper_2005_10445_gb300.binding import FskSearch, Runtime, rt_default_opts
+    s = FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp)
+    o = rt_default_opts(w.fs_hz)
+    for k, v in opt.items():
+        setattr(o, k, v)
+    return Runtime(s, periods, o), o
+
+
+def feed(rt, w, chunk):
+    evs = []
+    for a in range(0, w.n_samples, chunk):
+        rt.push(w.iq16[a:a + chunk])
+        evs.append(rt.pump())
+    return np.concatenate(evs)
+
+
+def oracle_block(w, start, length, code, toa_abs):
+    """The oracle's detection of `code` in the task block [start, start + length)
+    closest to toa_abs (windows around it only), in absolute samples."""
+    T = len(w.h_bp) + w.sps - 1
+    N, W, hop, n_c = fsk.plan(length, len(w.chips[code]), w.sps, T)
+    wi = min(int((toa_abs - start) // hop), W - 1)
+    pairs = [(k, code) for k in (wi - 1, wi, wi + 1) if 0 <= k < W]
+    dets, _ = fsk.search(w.iq16[start:start + length], w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz,
+                         w.h_bp, pairs=pairs)
+    assert dets, (start, length, code)
+    return min(dets, key=lambda d: abs(start + d.toa - toa_abs))
+
+
+def test_runtime_tracks_periodic_tags(torch_cuda):
+    from paper_2005_10445_gb300 import binding as b
+    w, periods = synth.fsk_periodic(seed=7)
+    rt, o = make_rt(w, periods)
+    ev = feed(rt, w, 160000)
+    st = rt.stats()
+    assert st["search_tasks"] >= 1 and st["track_tasks"] >= 10
+    assert not np.any(np.isin(ev["kind"], [b.RT_TRACK_MISS, b.RT_TRACK_LOST, b.RT_SEARCH_SKIPPED]))
+    L = len(w.chips[0]) * w.sps
+    for c in range(len(w.chips)):
+        mine = ev[ev["code"] == c]
+        # one searching task finds every transmission of its block (a block
+        # holds one to three periods), then tracking takes over
+        n_s = int(np.sum(mine["kind"] == b.RT_SEARCH_DETECTION))
+        assert n_s >= 1 and np.all(mine["kind"][:n_s] == b.RT_SEARCH_DETECTION)
+        assert len(set(mine["task_start"][:n_s].tolist())) == 1
+        assert len(mine) > n_s and np.all(mine["kind"][n_s:] == b.RT_TRACK_DETECTION)
+        truth = np.array([t.delay for t in w.tags if t.code == c])
+        for e in mine:  # each event is one of the code's transmissions, each reported once
+            assert np.min(np.abs(truth - e["toa"])) <= 2.0
+        hit = {int(np.argmin(np.abs(truth - e["toa"]))) for e in mine}
+        assert len(hit) == len(mine)
+        # every transmission after the first detection whose tracking block has arrived is reported
+        first = int(np.argmin(np.abs(truth - mine["toa"][0])))
+        margin = (o.track_block - (L + len(w.h_bp) + w.sps - 2)) // 2
+        due = [i for i in range(first, len(truth)) if truth[i] - margin + o.track_block <= w.n_samples - 3]
+        assert set(due) <= hit
+    assert st["search_units"] > 0 and st["track_units"] > 0 and st["searching"] == 0
+    # a searching detection and two tracking detections against the oracle on their blocks
+    picks = [ev[ev["kind"] == b.RT_SEARCH_DETECTION][0]] + list(ev[ev["kind"] == b.RT_TRACK_DETECTION][[0, -1]])
+    for e in picks:
+        length = o.search_block if e["kind"] == b.RT_SEARCH_DETECTION else o.track_block
+        d = oracle_block(w, int(e["task_start"]), length, int(e["code"]), float(e["toa"]))
+        assert abs(e["toa"] - (e["task_start"] + d.toa)) <= TOA_ATOL
+        assert e["score"] == pytest.approx(d.score, rel=SCORE_RTOL)
+        assert e["w_c"] == pytest.approx(d.w_c, rel=SUM_RTOL)
+        assert e["q"] == pytest.approx(d.q, rel=SUM_RTOL)
+
+
+def test_runtime_task_sequence_is_deterministic(torch_cuda):
+    """The same input gives the same events, bit for bit; other push sizes
+    change when tasks become ready, and so their order, but not the events."""
+    w, periods = synth.fsk_periodic(seed=8, seconds=0.5)
+    a = feed(make_rt(w, periods)[0], w, 160000)
+    a2 = feed(make_rt(w, periods)[0], w, 160000)
+    b_ = feed(make_rt(w, periods)[0], w, 100000)
+    assert len(a) > 5 and a.tobytes() == a2.tobytes()
+    key = lambda e: np.sort(e, order=["code", "toa"]).tobytes()
+    assert key(a) == key(b_)
+
+
+def test_runtime_reports_overruns(torch_cuda):
+    """A cyclic buffer of a little more than one searching block: pushing well
+    past it without processing skips searching blocks and loses the tracked
+    codes' predicted transmissions; processing resumes on the newest samples."""
+    from paper_2005_10445_gb300 import binding as b
+    w, periods = synth.fsk_periodic(seed=9, seconds=1.0)
+    o0 = b.rt_default_opts(w.fs_hz)
+    rt, o = make_rt(w, periods, ring_samples=o0.search_block + o0.track_block + 50000)
+    first = feed(rt, w.__class__(**{**w.__dict__, "iq16": w.iq16[:1200000]}), 200000)
+    assert np.any(first["kind"] == b.RT_SEARCH_DETECTION)
+    rt.push(w.iq16[1200000:3600000])   # 2.4 M samples, five times the buffer, unprocessed
+    ev = rt.pump()
+    kinds = set(ev["kind"].tolist())
+    assert b.RT_SEARCH_SKIPPED in kinds and b.RT_TRACK_LOST in kinds
+    rt.push(w.iq16[3600000:])
+    ev2 = rt.pump()
+    assert np.any(np.isin(ev2["kind"], [b.RT_SEARCH_DETECTION, b.RT_TRACK_DETECTION]))
