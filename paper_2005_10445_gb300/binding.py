@@ -36,6 +36,8 @@ EXPORTED = [
     "atlas_prop_features", "atlas_prop_loss_grad", "atlas_prop_adam", "atlas_prop_logits", "atlas_prop_candidates",
     "atlas_acq_run_proposed", "atlas_prop_last_error", "atlas_prop_destroy",
 ]
+# Every symbol include/atlas_unfused.h declares (the comparison pipeline).
+EXPORTED_UNFUSED = ["atlas_unfused_create", "atlas_unfused_run", "atlas_unfused_last_error", "atlas_unfused_destroy"]
 # Every symbol include/atlas_rt.h declares.
 EXPORTED_RT = [
     "atlas_rt_default_opts", "atlas_rt_create", "atlas_rt_push", "atlas_rt_pump", "atlas_rt_get_stats",
@@ -223,6 +225,14 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_fsk_last_error.restype = ctypes.c_char_p
     lib.atlas_fsk_destroy.argtypes = [vp]
     lib.atlas_fsk_destroy.restype = None
+    lib.atlas_unfused_create.argtypes = [ctypes.POINTER(vp), vp, vp, i32, i32, f64, vp, i32, i32, ctypes.c_float, i32]
+    lib.atlas_unfused_create.restype = ctypes.c_int
+    lib.atlas_unfused_run.argtypes = [vp, vp, vp, i64, vp, i32, vp]
+    lib.atlas_unfused_run.restype = ctypes.c_int
+    lib.atlas_unfused_last_error.argtypes = [vp]
+    lib.atlas_unfused_last_error.restype = ctypes.c_char_p
+    lib.atlas_unfused_destroy.argtypes = [vp]
+    lib.atlas_unfused_destroy.restype = None
     lib.atlas_rt_default_opts.argtypes = [ctypes.POINTER(RtOpts), f64]
     lib.atlas_rt_default_opts.restype = None
     lib.atlas_rt_create.argtypes = [ctypes.POINTER(vp), vp, vp, i32, ctypes.POINTER(RtOpts)]
@@ -675,6 +685,57 @@ class Runtime:
     def close(self) -> None:
         if self.ctx:
             self._lib.atlas_rt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# comparison pipeline (include/atlas_unfused.h): measurement baseline only
+# ---------------------------------------------------------------------------
+
+class UnfusedSearch:
+    """The coherent search organised like the paper's GPU implementation (cuFFT +
+    element-wise kernels, the correlation surface in device memory)."""
+
+    def __init__(self, chips: Sequence[np.ndarray], samples_per_chip: int, fs_hz: float,
+                 freq_offsets_hz: Sequence[float], threshold: float = 25.0, fft_len: int = 0,
+                 windows_per_launch: int = 0):
+        lib = load()
+        self._lib = lib
+        self.ctx = ctypes.c_void_p()
+        cat = np.ascontiguousarray(np.concatenate([np.asarray(c, np.int8) for c in chips]))
+        cpc = np.ascontiguousarray(np.array([len(c) for c in chips], np.int32))
+        fr = np.ascontiguousarray(np.asarray(freq_offsets_hz, np.float64))
+        st = lib.atlas_unfused_create(ctypes.byref(self.ctx), cat.ctypes.data, cpc.ctypes.data, len(chips),
+                                      samples_per_chip, float(fs_hz), fr.ctypes.data, len(fr), fft_len,
+                                      float(threshold), windows_per_launch)
+        if st != ATLAS_OK:
+            self.ctx = None
+        _check(st)
+
+    def run_ptr(self, stream: int, d_iq: int, n_samples: int, d_out: int, capacity: int, d_count: int) -> None:
+        st = self._lib.atlas_unfused_run(self.ctx, stream, d_iq, n_samples, d_out, capacity, d_count)
+        if st != ATLAS_OK:
+            raise AtlasError(st, strerror(st) + ": " + self._lib.atlas_unfused_last_error(self.ctx).decode())
+
+    def run(self, x_iq, capacity: int = 4096):
+        import torch
+        out = torch.zeros(max(capacity, 1) * 32, dtype=torch.uint8, device=x_iq.device)
+        cnt = torch.zeros(1, dtype=torch.int32, device=x_iq.device)
+        st = torch.cuda.current_stream(x_iq.device)
+        self.run_ptr(st.cuda_stream, x_iq.data_ptr(), x_iq.shape[0], out.data_ptr(), capacity, cnt.data_ptr())
+        st.synchronize()
+        n = int(cnt.item())
+        return out.cpu().numpy().view(DETECTION_DTYPE)[: min(n, capacity)].copy(), n
+
+    def close(self) -> None:
+        if self.ctx:
+            self._lib.atlas_unfused_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

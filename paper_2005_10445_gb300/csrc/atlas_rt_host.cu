@@ -44,6 +44,8 @@ struct atlas_rt {
 
 namespace {
 
+constexpr int kEagerRecords = 8;  // records read back with the count
+
 int fail_cuda(atlas_rt* rt, cudaError_t e) {
   if (rt) rt->last_error = cudaGetErrorString(e);
   return ATLAS_ERR_CUDA;
@@ -88,11 +90,16 @@ int run_block(atlas_rt* rt, cudaStream_t st, int64_t s, int64_t len, const std::
     rt->last_error = atlas_fsk_last_error(rt->fsk);
     return r;
   }
+  // the count and the first few records come back together (one synchronisation
+  // for a tracking task); more records, if there are more, after it
+  const int first = std::min(kEagerRecords, rt->o.capacity);
   CK(cudaMemcpyAsync(rt->h_count, rt->d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rt->h_out, rt->d_out, sizeof(atlas_fsk_detection) * (size_t)first, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int n = std::min(*rt->h_count, rt->o.capacity);
-  if (n > 0) {
-    CK(cudaMemcpyAsync(rt->h_out, rt->d_out, sizeof(atlas_fsk_detection) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  if (n > first) {
+    CK(cudaMemcpyAsync(rt->h_out + first, rt->d_out + first, sizeof(atlas_fsk_detection) * (size_t)(n - first),
+                       cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
   *n_det = n;

@@ -219,3 +219,20 @@ def test_rt_rejects_bad_arguments(lib):
     assert lib.atlas_rt_pump(None, None, 0, None, 0, ctypes.byref(n)) == E
     assert lib.atlas_rt_get_stats(None, None) == E
     lib.atlas_rt_destroy(None)
+
+
+def test_unfused_header_and_exports(lib):
+    src = open(os.path.join(ROOT, "include", "atlas_unfused.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = sorted(set(re.findall(r"\b(atlas_[a-z_]+)\s*\(", src)))
+    assert names == sorted(binding.EXPORTED_UNFUSED)
+    for name in names:
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+    ctx = ctypes.c_void_p()
+    ch = np.ones(200, np.int8)
+    cpc = np.array([100, 50], np.int32)
+    f = np.zeros(1)
+    assert lib.atlas_unfused_create(ctypes.byref(ctx), ch.ctypes.data, cpc.ctypes.data, 2, 2, 1e6, f.ctypes.data, 1,
+                                    0, 25.0, 0) == binding.ATLAS_ERR_UNSUPPORTED   # codes of two lengths
+    assert lib.atlas_unfused_run(None, None, None, 0, None, 0, None) == binding.ATLAS_ERR_INVALID_ARG
+    lib.atlas_unfused_destroy(None)
