@@ -225,6 +225,16 @@ int64_t atlas_prop_num_params(atlas_prop_t p);
 int atlas_prop_get_params(atlas_prop_t p, float* h_params);
 int atlas_prop_set_params(atlas_prop_t p, const float* h_params);
 
+/* Checkpoint: the FP32 parameters, the Adam moments and the step count in one
+ * file (little-endian): a 40-byte header -- magic "ATLPROP1", uint32 version 1,
+ * int32 n_codes, int32 n_bins, uint32 CRC-32 (IEEE 802.3) of the payload,
+ * int64 n_params, int64 step -- then params, m, v as float32 [n_params] each.
+ * Load checks the magic, version, shapes, length and CRC and returns
+ * ATLAS_ERR_INVALID_ARG on any mismatch, leaving the network unchanged;
+ * training resumes exactly where the saved run stood.  Synchronous. */
+int atlas_prop_save(atlas_prop_t p, const char* path);
+int atlas_prop_load(atlas_prop_t p, const char* path);
+
 /* Features of n_windows windows of window_len samples (a multiple of 4096) starting at
  * first_sample + w * stride of the device stream d_iq [n_samples][2]; samples outside
  * the stream read as zero.  d_feat: device [n_windows][4096]. */

@@ -33,6 +33,7 @@ EXPORTED = [
     "atlas_acq_profile_end", "atlas_acq_run_static", "atlas_acq_autotune", "atlas_acq_tuning",
     "atlas_acq_batch_create", "atlas_acq_batch_run", "atlas_acq_batch_kernels", "atlas_acq_batch_destroy",
     "atlas_prop_create", "atlas_prop_num_params", "atlas_prop_get_params", "atlas_prop_set_params",
+    "atlas_prop_save", "atlas_prop_load",
     "atlas_prop_features", "atlas_prop_loss_grad", "atlas_prop_adam", "atlas_prop_logits", "atlas_prop_candidates",
     "atlas_acq_run_proposed", "atlas_prop_last_error", "atlas_prop_destroy",
 ]
@@ -184,6 +185,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_prop_get_params.restype = ctypes.c_int
     lib.atlas_prop_set_params.argtypes = [vp, vp]
     lib.atlas_prop_set_params.restype = ctypes.c_int
+    lib.atlas_prop_save.argtypes = [vp, ctypes.c_char_p]
+    lib.atlas_prop_save.restype = ctypes.c_int
+    lib.atlas_prop_load.argtypes = [vp, ctypes.c_char_p]
+    lib.atlas_prop_load.restype = ctypes.c_int
     lib.atlas_prop_features.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp]
     lib.atlas_prop_features.restype = ctypes.c_int
     lib.atlas_prop_loss_grad.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
@@ -469,6 +474,12 @@ class Proposal:
         v = np.ascontiguousarray(v, np.float32)
         assert v.size == self.n_params
         self._chk(self._lib.atlas_prop_set_params(self.p, v.ctypes.data))
+
+    def save(self, path: str) -> None:
+        self._chk(self._lib.atlas_prop_save(self.p, path.encode()))
+
+    def load(self, path: str) -> None:
+        self._chk(self._lib.atlas_prop_load(self.p, path.encode()))
 
     def features(self, stream: int, d_iq: int, n_samples: int, first: int, stride: int, window_len: int,
                  n_windows: int, d_feat: int) -> None:

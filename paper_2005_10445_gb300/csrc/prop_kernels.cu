@@ -17,6 +17,7 @@
 // are bit-reproducible.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stdio.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -546,6 +547,78 @@ int atlas_prop_set_params(atlas_prop_t p, const float* h) {
   PCK(cudaMemset(p->m, 0, n * 4));
   PCK(cudaMemset(p->v, 0, n * 4));
   p->step = 0;
+  k_to_half<<<(unsigned)((n + 255) / 256), 256>>>(p->params, p->half, (int64_t)n);
+  PCK(cudaDeviceSynchronize());
+  return ATLAS_OK;
+}
+
+// CRC-32 of the IEEE 802.3 polynomial in its reflected form (0xEDB88320),
+// initial value and final xor 0xFFFFFFFF, bit by bit.
+static uint32_t crc32_update(uint32_t crc, const unsigned char* d, size_t n) {
+  for (size_t i = 0; i < n; ++i) {
+    crc ^= d[i];
+    for (int b = 0; b < 8; ++b) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+  }
+  return crc;
+}
+
+namespace {
+constexpr char kCkptMagic[8] = {'A', 'T', 'L', 'P', 'R', 'O', 'P', '1'};
+constexpr uint32_t kCkptVersion = 1;
+struct CkptHeader {  // 40 bytes, little-endian
+  char magic[8];
+  uint32_t version;
+  int32_t n_codes, n_bins;
+  uint32_t crc;      // of the payload: params, m, v (float32, n_params each)
+  int64_t n_params;
+  int64_t step;      // Adam steps taken
+};
+static_assert(sizeof(CkptHeader) == 40, "checkpoint header layout");
+}  // namespace
+
+int atlas_prop_save(atlas_prop_t p, const char* path) {
+  if (!p || !path) return ATLAS_ERR_INVALID_ARG;
+  const size_t n = p->lay.total;
+  std::vector<float> buf(3 * n);
+  PCK(cudaMemcpy(buf.data(), p->params, n * 4, cudaMemcpyDeviceToHost));
+  PCK(cudaMemcpy(buf.data() + n, p->m, n * 4, cudaMemcpyDeviceToHost));
+  PCK(cudaMemcpy(buf.data() + 2 * n, p->v, n * 4, cudaMemcpyDeviceToHost));
+  CkptHeader h;
+  memcpy(h.magic, kCkptMagic, 8);
+  h.version = kCkptVersion;
+  h.n_codes = p->lay.C;
+  h.n_bins = p->lay.K;
+  h.n_params = (int64_t)n;
+  h.step = p->step;
+  h.crc = crc32_update(0xFFFFFFFFu, reinterpret_cast<const unsigned char*>(buf.data()), buf.size() * 4) ^ 0xFFFFFFFFu;
+  FILE* f = fopen(path, "wb");
+  if (!f) return ATLAS_ERR_INVALID_ARG;
+  const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  const bool closed = fclose(f) == 0;
+  return ok && closed ? ATLAS_OK : ATLAS_ERR_INVALID_ARG;
+}
+
+int atlas_prop_load(atlas_prop_t p, const char* path) {
+  if (!p || !path) return ATLAS_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return ATLAS_ERR_INVALID_ARG;
+  CkptHeader h;
+  const size_t n = p->lay.total;
+  std::vector<float> buf(3 * n);
+  bool ok = fread(&h, sizeof(h), 1, f) == 1 && memcmp(h.magic, kCkptMagic, 8) == 0 && h.version == kCkptVersion &&
+            h.n_codes == p->lay.C && h.n_bins == p->lay.K && h.n_params == (int64_t)n && h.step >= 0 &&
+            fread(buf.data(), 4, buf.size(), f) == buf.size();
+  unsigned char extra;
+  ok = ok && fread(&extra, 1, 1, f) == 0;  // nothing after the payload
+  fclose(f);
+  if (!ok) return ATLAS_ERR_INVALID_ARG;
+  const uint32_t crc =
+      crc32_update(0xFFFFFFFFu, reinterpret_cast<const unsigned char*>(buf.data()), buf.size() * 4) ^ 0xFFFFFFFFu;
+  if (crc != h.crc) return ATLAS_ERR_INVALID_ARG;
+  PCK(cudaMemcpy(p->params, buf.data(), n * 4, cudaMemcpyHostToDevice));
+  PCK(cudaMemcpy(p->m, buf.data() + n, n * 4, cudaMemcpyHostToDevice));
+  PCK(cudaMemcpy(p->v, buf.data() + 2 * n, n * 4, cudaMemcpyHostToDevice));
+  p->step = h.step;
   k_to_half<<<(unsigned)((n + 255) / 256), 256>>>(p->params, p->half, (int64_t)n);
   PCK(cudaDeviceSynchronize());
   return ATLAS_OK;

@@ -236,3 +236,9 @@ def test_unfused_header_and_exports(lib):
                                     0, 25.0, 0) == binding.ATLAS_ERR_UNSUPPORTED   # codes of two lengths
     assert lib.atlas_unfused_run(None, None, None, 0, None, 0, None) == binding.ATLAS_ERR_INVALID_ARG
     lib.atlas_unfused_destroy(None)
+
+
+def test_prop_checkpoint_null_arguments(lib):
+    E = binding.ATLAS_ERR_INVALID_ARG
+    assert lib.atlas_prop_save(None, b"/nonexistent") == E
+    assert lib.atlas_prop_load(None, b"/nonexistent") == E
