@@ -371,6 +371,8 @@ def bandpass_taps(n_taps: int = 200, cutoff_hz: float = 1.5e6, fs_hz: float = 8e
     """A Hamming-windowed sinc low-pass of n_taps real taps: after the LO shift
     the transmissions' band is centred at zero, so the band-pass filter of the
     front end is a low-pass at baseband.  Unit gain at DC."""
+    if n_taps == 1:
+        return np.ones(1)
     n = np.arange(n_taps, dtype=np.float64)
     t = n - (n_taps - 1) / 2.0
     h = np.sinc(2.0 * cutoff_hz / fs_hz * t) * (0.54 - 0.46 * np.cos(2.0 * math.pi * n / (n_taps - 1)))

@@ -225,3 +225,32 @@ def test_realistic_full_size_sampled(torch_cuda):
     ora = oracle(w, pairs=sorted(pairs))
     sel = np.array([d for d in dets if (int(d["window"]), int(d["code"])) in pairs], dtype=dets.dtype)
     compare(sel, ora)
+
+
+@pytest.mark.parametrize("sps,fs,f1,f0,n_taps,fft_len,n_chips", [
+    (3, 3e6, 5e5, -5e5, 60, 0, 150),        # odd samples per chip
+    (2, 2e6, 3.5e5, -3.5e5, 30, 0, 400),    # tones that are not orthogonal over a chip
+    (4, 4e6, 5e5, -5e5, 1, 0, 150),         # a one-tap band-pass filter: T = sps
+    (4, 4e6, 5e5, -5e5, 40, 1024, 100),     # the smallest transform, 2^10
+])
+def test_fsk_shapes(torch_cuda, sps, fs, f1, f0, n_taps, fft_len, n_chips):
+    chips = [synth.random_chips(n_chips, 40 + c) for c in range(2)]
+    w = synth.fsk_stream(41, 30000, chips, sps, fs, f1, f0, -1.5e5, 3, (-6.0, 0.0), n_taps=n_taps,
+                         cutoff_hz=0.45 * fs, fft_len=fft_len)
+    _, dets, n = gpu_run(torch_cuda, w)
+    ora = oracle(w)
+    assert n == len(ora) >= 1
+    compare(dets, ora)
+
+
+def test_fsk_saturated_samples_and_zero_capacity(torch_cuda):
+    """Tags strong enough to clip the int16 range (both sides read the same
+    saturated samples), and a run with capacity 0 that only counts."""
+    w = synth.fsk_small(seed=15, snr_range=(22.0, 24.0))
+    assert np.abs(w.iq16.astype(np.int32)).max() == 32767 or w.iq16.min() == -32768
+    s, dets, n = gpu_run(torch_cuda, w)
+    ora = oracle(w)
+    assert n == len(ora) >= 1
+    compare(dets, ora)
+    _, none, n0 = gpu_run(torch_cuda, w, capacity=0)
+    assert n0 == n and len(none) == 0
