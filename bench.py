@@ -60,6 +60,29 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def fsk_ncu_traffic_per_cell():
+    """DRAM bytes per (window, code) cell of k_fsk_corr from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_fsk_corr_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in ("fsk_fft.cu", "acq_common.cuh", "fft_block.cuh"):
+        with open(os.path.join(ROOT, "paper_2005_10445_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+        return None
+    try:
+        return float(vals["dram_bytes_per_cell"])
+    except (KeyError, ValueError):
+        return None
+
+
 def ncu_traffic():
     """DRAM bytes per launch of the correlation kernel from the committed ncu
     summary, if it was taken on the current kernel source and launch size."""
@@ -576,7 +599,10 @@ def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
                    "l2": "flushed before each step (256 MiB write), outside the timed events",
                    "parallelism": "replicas: one independent stream per GPU", "detections_per_step": count},
         "roofline": {"bound": "alu", "achieved": dom[4], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": dom[4] / FP32_PEAK_TFLOPS, "traffic": None, "kernel": dom[0],
+                     "frac": dom[4] / FP32_PEAK_TFLOPS,
+                     "traffic": (fsk_ncu_traffic_per_cell() * corr_units
+                                 if dom[0].startswith("k_fsk_corr") and fsk_ncu_traffic_per_cell() else None),
+                     "kernel": dom[0],
                      "units_per_launch": dom[1], "flops_per_unit": dom[2], "avg_launch_ms": dom[3],
                      "kernel_share_of_step": dom[5],
                      "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, max clock)",

@@ -276,6 +276,26 @@ __global__ void __launch_bounds__(kFskSelectThreads) k_fsk_select(SelectParams p
 
 int64_t fsk_demod_outputs_per_block(int T) { return (int64_t)(1 << kFskLogB) - (T - 1); }
 
+namespace {
+
+// Co-resident blocks of `kern` on the current device (occupancy query, cached per device).
+template <class K>
+int resident_blocks(K kern, int threads, size_t smem) {
+  constexpr int kMaxDevices = 64;
+  static int cache[kMaxDevices] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < kMaxDevices && cache[dev] > 0) return cache[dev];
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  const int n = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  if (dev >= 0 && dev < kMaxDevices) cache[dev] = n;
+  return n;
+}
+
+}  // namespace
+
 cudaError_t fsk_prepare() {
   cudaError_t e = cudaFuncSetAttribute(k_fsk_demod, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fsk_demod_smem());
@@ -288,14 +308,7 @@ cudaError_t launch_fsk_demod(const FskDemodParams& p, cudaStream_t s) {
   if (p.T < 1 || p.T > kFskMaxTaps) return cudaErrorInvalidValue;
   const int64_t per = fsk_demod_outputs_per_block(p.T);
   const int64_t blocks = (p.count + per - 1) / per + 1;  // the grid of blocks may straddle one more
-  static int resident = 0;
-  if (resident == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsk_demod, kFskDemodThreads, fsk_demod_smem());
-    resident = sms * (per_sm > 0 ? per_sm : 1);
-  }
+  const int resident = resident_blocks(k_fsk_demod, kFskDemodThreads, fsk_demod_smem());
   const int grid = (int)(blocks < resident ? blocks : resident);
   k_fsk_demod<<<grid, kFskDemodThreads, fsk_demod_smem(), s>>>(p);
   return cudaGetLastError();
@@ -316,7 +329,8 @@ cudaError_t launch_fsk_select(const SelectParams& p, cudaStream_t s) {
 cudaError_t launch_fsk_stats(const FskStatsParams& p, int max_cand, cudaStream_t s) {
   if (max_cand > 0) {
     const int items = max_cand * kFskStatsSlices;
-    k_fsk_stats_part<<<items < 1216 ? items : 1216, kFskStatsThreads, 0, s>>>(p);
+    const int resident = resident_blocks(k_fsk_stats_part, kFskStatsThreads, 0);
+    k_fsk_stats_part<<<items < resident ? items : resident, kFskStatsThreads, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_fsk_stats_final<<<(max_cand + kFskStatsThreads - 1) / kFskStatsThreads, kFskStatsThreads, 0, s>>>(p);
