@@ -137,6 +137,28 @@ int atlas_fsk_demod(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t 
  * floats; *n gets n_c. */
 int atlas_fsk_code_demod(atlas_fsk_t ctx, int32_t code, float* h_dc, int32_t cap, int32_t* n);
 
+/*
+ * Tracking task as a single launch.  A tracker replays one CUDA graph, captured
+ * at creation, that searches one code on a block of n_samples samples taken
+ * straight out of a cyclic buffer of int16 (I, Q) pairs: absolute sample i is
+ * d_ring[i mod ring_samples].  The block's start, and with it the LO phase of
+ * step 2, and the code are written into a 16-byte device descriptor by the
+ * graph's first node.  A tracker serves the codes whose length equals `code`'s.
+ *   d_ring        device, caller-owned, must outlive the tracker
+ *   n_samples     block length, >= the codes' support n_c
+ * atlas_fsk_tracker_run is synchronous: one graph launch on `stream`, one
+ * synchronisation; h_out (host, capacity records) receives the detections
+ * (windows, lags and ToAs relative to block_start), *h_count their number.
+ * The tracker uses the context's workspaces: it and the context's other calls
+ * must be ordered on one stream.
+ */
+typedef struct atlas_fsk_tracker* atlas_fsk_tracker_t;
+int atlas_fsk_tracker_create(atlas_fsk_tracker_t* out, atlas_fsk_t ctx, int32_t code, int64_t n_samples,
+                             const int16_t* d_ring, int64_t ring_samples);
+int atlas_fsk_tracker_run(atlas_fsk_tracker_t t, void* stream, int32_t code, int64_t block_start,
+                          atlas_fsk_detection* h_out, int32_t capacity, int32_t* h_count);
+void atlas_fsk_tracker_destroy(atlas_fsk_tracker_t t);
+
 /* Device-time profile of the runs between begin and end: CUDA events on the
  * run's stream around the demodulation and correlation launches (at most
  * max_timed of each kind are timed; the counts cover every launch). */

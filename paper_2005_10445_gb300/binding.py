@@ -49,6 +49,7 @@ EXPORTED_FSK = [
     "atlas_fsk_default_opts", "atlas_fsk_create", "atlas_fsk_windows", "atlas_fsk_run", "atlas_fsk_run_codes",
     "atlas_fsk_run_host",
     "atlas_fsk_demod", "atlas_fsk_code_demod", "atlas_fsk_profile_begin", "atlas_fsk_profile_end",
+    "atlas_fsk_tracker_create", "atlas_fsk_tracker_run", "atlas_fsk_tracker_destroy",
     "atlas_fsk_last_error", "atlas_fsk_destroy",
 ]
 
@@ -226,6 +227,12 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_fsk_profile_begin.restype = ctypes.c_int
     lib.atlas_fsk_profile_end.argtypes = [vp, ctypes.POINTER(FskProfile)]
     lib.atlas_fsk_profile_end.restype = ctypes.c_int
+    lib.atlas_fsk_tracker_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64, vp, i64]
+    lib.atlas_fsk_tracker_create.restype = ctypes.c_int
+    lib.atlas_fsk_tracker_run.argtypes = [vp, vp, i32, i64, vp, i32, ctypes.POINTER(i32)]
+    lib.atlas_fsk_tracker_run.restype = ctypes.c_int
+    lib.atlas_fsk_tracker_destroy.argtypes = [vp]
+    lib.atlas_fsk_tracker_destroy.restype = None
     lib.atlas_fsk_last_error.argtypes = [vp]
     lib.atlas_fsk_last_error.restype = ctypes.c_char_p
     lib.atlas_fsk_destroy.argtypes = [vp]
@@ -748,6 +755,36 @@ class UnfusedSearch:
         if self.ctx:
             self._lib.atlas_unfused_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FskTracker:
+    """atlas_fsk_tracker_*: one code on a block of a device cyclic buffer, one graph launch."""
+
+    def __init__(self, fsk: FskSearch, code: int, n_samples: int, d_ring: int, ring_samples: int):
+        lib = load()
+        self._lib = lib
+        self.fsk = fsk
+        self.t = ctypes.c_void_p()
+        _check_fsk(lib.atlas_fsk_tracker_create(ctypes.byref(self.t), fsk.ctx, code, n_samples, d_ring,
+                                                ring_samples), fsk.ctx)
+
+    def run(self, code: int, block_start: int, capacity: int = 64, stream: int = 0):
+        out = np.zeros(max(capacity, 1), FSK_DETECTION_DTYPE)
+        n = ctypes.c_int32()
+        _check_fsk(self._lib.atlas_fsk_tracker_run(self.t, stream, code, block_start, out.ctypes.data, capacity,
+                                                   ctypes.byref(n)), self.fsk.ctx)
+        return out[: min(n.value, capacity)].copy(), n.value
+
+    def close(self) -> None:
+        if self.t:
+            self._lib.atlas_fsk_tracker_destroy(self.t)
+            self.t = None
 
     def __del__(self):
         try:

@@ -367,6 +367,127 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   return ATLAS_OK;
 }
 
+// Where a launch group's raw samples come from: a linear device stream whose
+// sample 0 is absolute index first_sample, or a cyclic buffer read at the
+// device-side block start *ring_start.
+struct SampleSource {
+  const int16_t* iq = nullptr;
+  int64_t first_sample = 0;
+  const int16_t* ring = nullptr;
+  int64_t ring_cap = 0;
+  const int64_t* ring_start = nullptr;
+};
+
+// One launch group of one code-length group: windows [w0, w0 + nw) of a block
+// of S samples, Cg codes (device lists of their group-local indices and global
+// ids), records appended to d_out / d_count.  timed: CUDA events may be recorded
+// (not while a graph is being captured).
+int enqueue_group(atlas_fsk_ctx* ctx, cudaStream_t st, const FskGroup& g, int W, int w0, int nw, int64_t S,
+                  const SampleSource& src, int Cg, const int* d_sel_local, const int* d_sel_global,
+                  atlas_fsk_detection* d_out, int capacity, int* d_count, bool timed) {
+  // demodulated range of the group's windows, one sample of margin on each
+  // side for the neighbours of the interpolation
+  const int64_t base = (int64_t)w0 * g.hop - 1;
+  const int64_t len = (int64_t)(nw - 1) * g.hop + g.N + 2;
+  atlas::FskDemodParams dp;
+  dp.iq = src.iq;
+  dp.ring = src.ring;
+  dp.ring_cap = src.ring_cap;
+  dp.ring_start = src.ring_start;
+  dp.S = S;
+  dp.S_out = S;
+  dp.start = base;
+  dp.count = len;
+  dp.T = ctx->T;
+  dp.lo_inc = ctx->lo_inc;
+  dp.lo_first = src.first_sample;
+  dp.G1 = ctx->d_G1;
+  dp.G0 = ctx->d_G0;
+  dp.tw = ctx->d_tw.at(atlas::kFskLogB);
+  dp.d = ctx->d_dbuf;
+  dp.u = ctx->d_ubuf;
+  const bool td = timed && ctx->profiling && 2 * ctx->demod_used + 1 < (int)ctx->ev_demod.size();
+  if (td) CK(cudaEventRecord(ctx->ev_demod[2 * ctx->demod_used], st));
+  CK(atlas::launch_fsk_demod(dp, st));
+  if (td) CK(cudaEventRecord(ctx->ev_demod[2 * ctx->demod_used++ + 1], st));
+  atlas::FskFwdParams fp;
+  fp.d = ctx->d_dbuf;
+  fp.base = base;
+  fp.len = len;
+  fp.hop = g.hop;
+  fp.w0 = w0;
+  fp.nw = nw;
+  fp.n_items = (nw + 1) / 2;
+  fp.tw = g.d_tw;
+  fp.twN = g.d_twN;
+  fp.X = ctx->d_X;
+  fp.scale = 1.0f;
+  fp.conj_out = 0;
+  CK(atlas::launch_fsk_fwd(g.logN, fp, st));
+  atlas::FskCorrParams cp;
+  cp.X = ctx->d_X;
+  cp.C = g.d_spec;
+  cp.tw = g.d_tw;
+  cp.twN = g.d_twN;
+  cp.part = ctx->d_part;
+  cp.S = S;
+  cp.N = g.N;
+  cp.hop = g.hop;
+  cp.W = W;
+  cp.n_c = g.n_c;
+  cp.w0 = w0;
+  cp.nw = nw;
+  cp.Cg = Cg;
+  cp.sel = d_sel_local;
+  const bool tc = timed && ctx->profiling && 2 * ctx->corr_used + 1 < (int)ctx->ev_corr.size();
+  if (tc) CK(cudaEventRecord(ctx->ev_corr[2 * ctx->corr_used], st));
+  CK(atlas::launch_fsk_corr(g.logN, cp, st));
+  if (tc) CK(cudaEventRecord(ctx->ev_corr[2 * ctx->corr_used++ + 1], st));
+  if (timed && ctx->profiling) {
+    ctx->prof.launches += 7;  // demod, forward, corr, select, two stats kernels, advance
+    ctx->prof.corr_launches += 1;
+    ctx->prof.corr_units += (int64_t)nw * Cg;
+    ctx->prof.demod_launches += 1;
+    ctx->prof.demod_samples += len;
+  }
+  CK(cudaMemsetAsync(ctx->d_ncand, 0, sizeof(int), st));
+  atlas::SelectParams sp;
+  sp.part = ctx->d_part;
+  sp.codes = d_sel_global;
+  sp.Cg = Cg;
+  sp.C = ctx->C;
+  sp.K = 1;
+  sp.sps = g.R;
+  sp.N = g.N;
+  sp.W = W;
+  sp.w0 = w0;
+  sp.nw = nw;
+  sp.threshold = ctx->threshold;
+  sp.out = ctx->d_cand;
+  sp.capacity = nw * Cg;
+  sp.count = ctx->d_ncand;
+  sp.cells = nullptr;
+  CK(atlas::launch_fsk_select(sp, st));
+  atlas::FskStatsParams tp;
+  tp.cand = ctx->d_cand;
+  tp.n_cand = ctx->d_ncand;
+  tp.d = ctx->d_dbuf;
+  tp.u = ctx->d_ubuf;
+  tp.base = base;
+  tp.len = len;
+  tp.dc = ctx->d_dc;
+  tp.ld = ctx->max_nc;
+  tp.n_c = g.n_c;
+  tp.hop = g.hop;
+  tp.S = S;
+  tp.out = d_out;
+  tp.capacity = capacity;
+  tp.count = d_count;
+  tp.part = ctx->d_stats_part;
+  CK(atlas::launch_fsk_stats(tp, nw * Cg, st));
+  return ATLAS_OK;
+}
+
 // sel: host list of the searched codes (n_sel of them), or null for every code.
 int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S, int64_t first_sample,
              const int32_t* sel, int n_sel, atlas_fsk_detection* d_out, int capacity, int* d_count) {
@@ -397,7 +518,9 @@ int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S
     }
   }
   CK(cudaMemsetAsync(d_count, 0, sizeof(int), st));
-  const float2* twB = ctx->d_tw.at(atlas::kFskLogB);
+  SampleSource src;
+  src.iq = d_iq;
+  src.first_sample = first_sample;
   for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
     const FskGroup& g = ctx->groups[gi];
     const int W = g.windows(S);
@@ -406,104 +529,9 @@ int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S
     const int* d_sel_local = sel ? ctx->d_sel + sel_off[gi] : nullptr;
     const int* d_sel_global = sel ? ctx->d_sel + sel_off[gi] + Cg : g.d_codes;
     for (int w0 = 0; w0 < W; w0 += ctx->wc) {
-      const int nw = std::min(ctx->wc, W - w0);
-      // demodulated range of the group's windows, one sample of margin on each
-      // side for the neighbours of the interpolation
-      const int64_t base = (int64_t)w0 * g.hop - 1;
-      const int64_t len = (int64_t)(nw - 1) * g.hop + g.N + 2;
-      atlas::FskDemodParams dp;
-      dp.iq = d_iq;
-      dp.S = S;
-      dp.S_out = S;
-      dp.start = base;
-      dp.count = len;
-      dp.T = ctx->T;
-      dp.lo_inc = ctx->lo_inc;
-      dp.lo_first = first_sample;
-      dp.G1 = ctx->d_G1;
-      dp.G0 = ctx->d_G0;
-      dp.tw = twB;
-      dp.d = ctx->d_dbuf;
-      dp.u = ctx->d_ubuf;
-      const bool td = ctx->profiling && 2 * ctx->demod_used + 1 < (int)ctx->ev_demod.size();
-      if (td) CK(cudaEventRecord(ctx->ev_demod[2 * ctx->demod_used], st));
-      CK(atlas::launch_fsk_demod(dp, st));
-      if (td) CK(cudaEventRecord(ctx->ev_demod[2 * ctx->demod_used++ + 1], st));
-      atlas::FskFwdParams fp;
-      fp.d = ctx->d_dbuf;
-      fp.base = base;
-      fp.len = len;
-      fp.hop = g.hop;
-      fp.w0 = w0;
-      fp.nw = nw;
-      fp.n_items = (nw + 1) / 2;
-      fp.tw = g.d_tw;
-      fp.twN = g.d_twN;
-      fp.X = ctx->d_X;
-      fp.scale = 1.0f;
-      fp.conj_out = 0;
-      CK(atlas::launch_fsk_fwd(g.logN, fp, st));
-      atlas::FskCorrParams cp;
-      cp.X = ctx->d_X;
-      cp.C = g.d_spec;
-      cp.tw = g.d_tw;
-      cp.twN = g.d_twN;
-      cp.part = ctx->d_part;
-      cp.S = S;
-      cp.N = g.N;
-      cp.hop = g.hop;
-      cp.W = W;
-      cp.n_c = g.n_c;
-      cp.w0 = w0;
-      cp.nw = nw;
-      cp.Cg = Cg;
-      cp.sel = d_sel_local;
-      const bool tc = ctx->profiling && 2 * ctx->corr_used + 1 < (int)ctx->ev_corr.size();
-      if (tc) CK(cudaEventRecord(ctx->ev_corr[2 * ctx->corr_used], st));
-      CK(atlas::launch_fsk_corr(g.logN, cp, st));
-      if (tc) CK(cudaEventRecord(ctx->ev_corr[2 * ctx->corr_used++ + 1], st));
-      if (ctx->profiling) {
-        ctx->prof.launches += 7;  // demod, forward, corr, select, two stats kernels, advance
-        ctx->prof.corr_launches += 1;
-        ctx->prof.corr_units += (int64_t)nw * Cg;
-        ctx->prof.demod_launches += 1;
-        ctx->prof.demod_samples += len;
-      }
-      CK(cudaMemsetAsync(ctx->d_ncand, 0, sizeof(int), st));
-      atlas::SelectParams sp;
-      sp.part = ctx->d_part;
-      sp.codes = d_sel_global;
-      sp.Cg = Cg;
-      sp.C = ctx->C;
-      sp.K = 1;
-      sp.sps = g.R;
-      sp.N = g.N;
-      sp.W = W;
-      sp.w0 = w0;
-      sp.nw = nw;
-      sp.threshold = ctx->threshold;
-      sp.out = ctx->d_cand;
-      sp.capacity = nw * Cg;
-      sp.count = ctx->d_ncand;
-      sp.cells = nullptr;
-      CK(atlas::launch_fsk_select(sp, st));
-      atlas::FskStatsParams tp;
-      tp.cand = ctx->d_cand;
-      tp.n_cand = ctx->d_ncand;
-      tp.d = ctx->d_dbuf;
-      tp.u = ctx->d_ubuf;
-      tp.base = base;
-      tp.len = len;
-      tp.dc = ctx->d_dc;
-      tp.ld = ctx->max_nc;
-      tp.n_c = g.n_c;
-      tp.hop = g.hop;
-      tp.S = S;
-      tp.out = d_out;
-      tp.capacity = capacity;
-      tp.count = d_count;
-      tp.part = ctx->d_stats_part;
-      CK(atlas::launch_fsk_stats(tp, nw * Cg, st));
+      const int r = enqueue_group(ctx, st, g, W, w0, std::min(ctx->wc, W - w0), S, src, Cg, d_sel_local,
+                                  d_sel_global, d_out, capacity, d_count, true);
+      if (r != ATLAS_OK) return r;
     }
   }
   return ATLAS_OK;
@@ -511,7 +539,130 @@ int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S
 
 }  // namespace
 
+struct atlas_fsk_tracker {
+  atlas_fsk_ctx* ctx = nullptr;
+  int gi = 0;         // code-length group
+  int64_t len = 0;    // block samples
+  int W = 0;          // windows of a block
+  struct Desc {       // read by the graph's kernels
+    int64_t start;    // absolute index of the block's first sample
+    int32_t local;    // the code's index within its group
+    int32_t global;   // the code
+  };
+  Desc* h_desc = nullptr;  // pinned: copied in by the graph's first node
+  Desc* d_desc = nullptr;
+  atlas_fsk_detection* d_out = nullptr;
+  int* d_count = nullptr;
+  atlas_fsk_detection* h_out = nullptr;  // pinned: copied out by the graph's last nodes
+  int* h_count = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void free_tracker(atlas_fsk_tracker* t) {
+  if (!t) return;
+  if (t->exec) cudaGraphExecDestroy(t->exec);
+  if (t->graph) cudaGraphDestroy(t->graph);
+  if (t->cs) cudaStreamDestroy(t->cs);
+  cudaFreeHost(t->h_desc);
+  cudaFreeHost(t->h_out);
+  cudaFreeHost(t->h_count);
+  cudaFree(t->d_desc);
+  cudaFree(t->d_out);
+  cudaFree(t->d_count);
+  delete t;
+}
+
+int capture_tracker(atlas_fsk_tracker* t, const int16_t* d_ring, int64_t ring_samples) {
+  atlas_fsk_ctx* ctx = t->ctx;
+  const FskGroup& g = ctx->groups[t->gi];
+  cudaStream_t cs = t->cs;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  SampleSource src;
+  src.ring = d_ring;
+  src.ring_cap = ring_samples;
+  src.ring_start = &t->d_desc->start;
+  int r = ATLAS_OK;
+  cudaError_t e = cudaMemcpyAsync(t->d_desc, t->h_desc, sizeof(atlas_fsk_tracker::Desc), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->d_count, 0, sizeof(int), cs);
+  for (int w0 = 0; e == cudaSuccess && r == ATLAS_OK && w0 < t->W; w0 += ctx->wc)
+    r = enqueue_group(ctx, cs, g, t->W, w0, std::min(ctx->wc, t->W - w0), t->len, src, 1, &t->d_desc->local,
+                      &t->d_desc->global, t->d_out, t->W, t->d_count, false);
+  if (e == cudaSuccess && r == ATLAS_OK)
+    e = cudaMemcpyAsync(t->h_count, t->d_count, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && r == ATLAS_OK)
+    e = cudaMemcpyAsync(t->h_out, t->d_out, sizeof(atlas_fsk_detection) * (size_t)t->W, cudaMemcpyDeviceToHost, cs);
+  const cudaError_t e_end = cudaStreamEndCapture(cs, &t->graph);  // always leaves capture mode
+  if (r != ATLAS_OK) return r;
+  if (e != cudaSuccess) return fail_cuda(ctx, e);
+  if (e_end != cudaSuccess) return fail_cuda(ctx, e_end);
+  CK(cudaGraphInstantiate(&t->exec, t->graph, 0));
+  return ATLAS_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int atlas_fsk_tracker_create(atlas_fsk_tracker_t* out, atlas_fsk_t ctx, int32_t code, int64_t n_samples,
+                             const int16_t* d_ring, int64_t ring_samples) {
+  if (!out) return ATLAS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ctx || code < 0 || code >= ctx->C || !d_ring || ring_samples < n_samples) return ATLAS_ERR_INVALID_ARG;
+  const int gi = ctx->code_group[code];
+  const FskGroup& g = ctx->groups[gi];
+  if (n_samples < g.n_c || n_samples > ((int64_t)1 << 31)) return ATLAS_ERR_INVALID_ARG;
+  atlas_fsk_tracker* t = new (std::nothrow) atlas_fsk_tracker();
+  if (!t) return ATLAS_ERR_NO_MEMORY;
+  t->ctx = ctx;
+  t->gi = gi;
+  t->len = n_samples;
+  t->W = g.windows(n_samples);
+  if (cudaMallocHost((void**)&t->h_desc, sizeof(atlas_fsk_tracker::Desc)) != cudaSuccess ||
+      cudaMallocHost((void**)&t->h_out, sizeof(atlas_fsk_detection) * (size_t)t->W) != cudaSuccess ||
+      cudaMallocHost((void**)&t->h_count, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&t->d_desc, sizeof(atlas_fsk_tracker::Desc)) != cudaSuccess ||
+      cudaMalloc((void**)&t->d_out, sizeof(atlas_fsk_detection) * (size_t)t->W) != cudaSuccess ||
+      cudaMalloc((void**)&t->d_count, sizeof(int)) != cudaSuccess) {
+    free_tracker(t);
+    return ATLAS_ERR_NO_MEMORY;
+  }
+  memset(t->h_desc, 0, sizeof(atlas_fsk_tracker::Desc));
+  int r = ATLAS_OK;
+  if (cudaStreamCreateWithFlags(&t->cs, cudaStreamNonBlocking) != cudaSuccess) r = ATLAS_ERR_CUDA;
+  if (r == ATLAS_OK) r = capture_tracker(t, d_ring, ring_samples);
+  if (r != ATLAS_OK) {
+    free_tracker(t);
+    return r;
+  }
+  *out = t;
+  return ATLAS_OK;
+}
+
+int atlas_fsk_tracker_run(atlas_fsk_tracker_t t, void* stream, int32_t code, int64_t block_start,
+                          atlas_fsk_detection* h_out, int32_t capacity, int32_t* h_count) {
+  if (!t || !h_count || capacity < 0 || (capacity > 0 && !h_out) || block_start < 0) return ATLAS_ERR_INVALID_ARG;
+  atlas_fsk_ctx* ctx = t->ctx;
+  if (code < 0 || code >= ctx->C || ctx->code_group[code] != t->gi) return ATLAS_ERR_INVALID_ARG;
+  const FskGroup& g = ctx->groups[t->gi];
+  int local = 0;
+  while (g.codes[local] != code) ++local;
+  t->h_desc->start = block_start;
+  t->h_desc->local = local;
+  t->h_desc->global = code;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaGraphLaunch(t->exec, st));
+  CK(cudaStreamSynchronize(st));  // the descriptor has been read, the results are in
+  const int n = std::min(*t->h_count, std::min(capacity, t->W));
+  if (n > 0) memcpy(h_out, t->h_out, sizeof(atlas_fsk_detection) * (size_t)n);
+  *h_count = *t->h_count;
+  return ATLAS_OK;
+}
+
+void atlas_fsk_tracker_destroy(atlas_fsk_tracker_t t) { free_tracker(t); }
 
 void atlas_fsk_default_opts(atlas_fsk_opts* o) {
   if (!o) return;

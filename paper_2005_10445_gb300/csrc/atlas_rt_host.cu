@@ -1,9 +1,10 @@
 // atlas_rt_host.cu -- continuous ingest (a cyclic buffer of int16 samples in
 // device memory) and the high-level scheduler of Section 2.2 (searching and
 // tracking tasks, half of the work each in an amortised sense), built on the
-// FSK search's C ABI (atlas_fsk_run_codes).  Host code only: every task is a
-// search run of the FSK front end's kernels on one block copied out of the
-// cyclic buffer.
+// FSK search's C ABI.  Host code only: a searching task is a search run
+// (atlas_fsk_run_codes) on one block copied out of the cyclic buffer; a
+// tracking task is one launch of a captured graph that reads its block from the
+// cyclic buffer directly (atlas_fsk_tracker_run).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -11,6 +12,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -39,6 +41,8 @@ struct atlas_rt {
   std::vector<double> pred;      // predicted arrival of its next transmission (absolute samples)
   std::vector<int> misses;
   atlas_rt_stats st = {};
+  // one single-launch tracker (captured graph) per support length, made on first use
+  std::map<int, atlas_fsk_tracker_t> trackers;
   std::string last_error;
 };
 
@@ -59,6 +63,7 @@ int fail_cuda(atlas_rt* rt, cudaError_t e) {
 
 void free_rt(atlas_rt* rt) {
   if (!rt) return;
+  for (auto& kv : rt->trackers) atlas_fsk_tracker_destroy(kv.second);
   cudaFree(rt->d_ring);
   cudaFree(rt->d_stage);
   cudaFree(rt->d_out);
@@ -103,6 +108,28 @@ int run_block(atlas_rt* rt, cudaStream_t st, int64_t s, int64_t len, const std::
     CK(cudaStreamSynchronize(st));
   }
   *n_det = n;
+  return ATLAS_OK;
+}
+
+// A tracking task: one graph launch that reads its block straight from the
+// cyclic buffer; the records land in h_out.
+int run_track(atlas_rt* rt, cudaStream_t st, int c, int64_t s, int* n_det) {
+  atlas_fsk_tracker_t& t = rt->trackers[rt->n_c[c]];
+  if (!t) {
+    const int r = atlas_fsk_tracker_create(&t, rt->fsk, c, rt->o.track_block, rt->d_ring, rt->cap);
+    if (r != ATLAS_OK) {
+      rt->last_error = atlas_fsk_last_error(rt->fsk);
+      t = nullptr;
+      return r;
+    }
+  }
+  int32_t n = 0;
+  const int r = atlas_fsk_tracker_run(t, st, c, s, rt->h_out, rt->o.capacity, &n);
+  if (r != ATLAS_OK) {
+    rt->last_error = atlas_fsk_last_error(rt->fsk);
+    return r;
+  }
+  *n_det = std::min<int>(n, rt->o.capacity);
   return ATLAS_OK;
 }
 
@@ -261,7 +288,7 @@ int atlas_rt_pump(atlas_rt_t rt, void* stream, int32_t max_tasks, atlas_rt_event
     if (do_track) {
       const int64_t s = track_start(rt, tc);
       int n = 0;
-      const int r = run_block(rt, st, s, TB, std::vector<int>{tc}, &n);
+      const int r = run_track(rt, st, tc, s, &n);
       if (r != ATLAS_OK) return r;
       rt->st.track_ms += elapsed_ms();
       rt->st.track_tasks += 1;

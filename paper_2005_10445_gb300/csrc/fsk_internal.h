@@ -33,6 +33,12 @@ struct FskDemodParams {
   int T;                        // composed filter taps
   uint64_t lo_inc;              // LO phase per sample, turns * 2^64 (x * exp(-j 2 pi f_lo i / fs))
   int64_t lo_first = 0;         // absolute stream index of input sample 0 (the LO phase continues across calls)
+  // Cyclic-buffer input (tracking tasks): when ring is set, input sample i is
+  // ring[(*ring_start + i) mod ring_cap] and lo_first is *ring_start (both read on
+  // the device, so a captured graph can be replayed for any block).
+  const int16_t* ring = nullptr;
+  int64_t ring_cap = 0;
+  const int64_t* ring_start = nullptr;
   const float2* G1;             // [B] FFT_B(g_1 zero padded) / B
   const float2* G0;             // [B]
   const float2* tw;             // twiddle tables of B

@@ -51,6 +51,9 @@ __global__ void __launch_bounds__(kFskDemodThreads) k_fsk_demod(FskDemodParams p
   const int64_t end = p.start + p.count;
   const int64_t n_blocks = (end - first + per - 1) / per;
   const short2* iq = reinterpret_cast<const short2*>(p.iq);
+  const short2* ring = reinterpret_cast<const short2*>(p.ring);
+  const int64_t ring_base = ring ? *p.ring_start : 0;
+  const int64_t lo_first = ring ? ring_base : p.lo_first;
   for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
     __syncthreads();  // tables ready; the previous block is done with Xs and A1
     // transform position n holds input sample i0 + n; outputs n >= T - 1 are
@@ -60,13 +63,16 @@ __global__ void __launch_bounds__(kFskDemodThreads) k_fsk_demod(FskDemodParams p
       const int64_t i = i0 + n;
       if (i < 0 || i >= p.S) return make_float2(0.f, 0.f);
       float2 x;
-      if (iq) {
+      if (ring) {
+        const short2 v = ring[(ring_base + i) % p.ring_cap];
+        x = make_float2((float)v.x, (float)v.y);
+      } else if (iq) {
         const short2 v = iq[i];
         x = make_float2((float)v.x, (float)v.y);
       } else {
         x = p.xf[i];
       }
-      if (p.lo_inc) x = cmul(x, expi_neg((uint64_t)(i + p.lo_first) * p.lo_inc));
+      if (p.lo_inc) x = cmul(x, expi_neg((uint64_t)(i + lo_first) * p.lo_inc));
       return x;
     };
     auto keep = [&](int k, float2 v) { Xs[k] = v; };

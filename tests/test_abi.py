@@ -242,3 +242,12 @@ def test_prop_checkpoint_null_arguments(lib):
     E = binding.ATLAS_ERR_INVALID_ARG
     assert lib.atlas_prop_save(None, b"/nonexistent") == E
     assert lib.atlas_prop_load(None, b"/nonexistent") == E
+
+
+def test_fsk_tracker_null_arguments(lib):
+    E = binding.ATLAS_ERR_INVALID_ARG
+    t = ctypes.c_void_p()
+    assert lib.atlas_fsk_tracker_create(ctypes.byref(t), None, 0, 1000, None, 1000) == E and not t.value
+    n = ctypes.c_int32()
+    assert lib.atlas_fsk_tracker_run(None, None, 0, 0, None, 0, ctypes.byref(n)) == E
+    lib.atlas_fsk_tracker_destroy(None)

@@ -119,3 +119,39 @@ def test_runtime_reports_overruns(torch_cuda):
     rt.push(w.iq16[3600000:])
     ev2 = rt.pump()
     assert np.any(np.isin(ev2["kind"], [b.RT_SEARCH_DETECTION, b.RT_TRACK_DETECTION]))
+
+
+def test_tracker_single_launch_equals_block_search(torch_cuda):
+    """The tracker's one graph launch, reading its block out of a cyclic buffer
+    (blocks that wrap around the buffer's end included), reports exactly what
+    a search of the same code on the same block copied out linearly reports."""
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import FSK_DETECTION_DTYPE, FskSearch, FskTracker
+    w, periods = synth.fsk_periodic(seed=10, seconds=0.3)
+    s = FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp)
+    ring_n, base, tb = 200000, 700000, 48000
+    ring = np.zeros((ring_n, 2), np.int16)
+    ring[np.arange(base, base + ring_n) % ring_n] = w.iq16[base:base + ring_n]
+    d_ring = torch.from_numpy(ring).cuda()
+    n_c = s.windows(0, tb)[3]
+    margin = (tb - n_c) // 2
+    starts = [(t.code, int(t.delay) - margin) for t in w.tags
+              if base <= int(t.delay) - margin and int(t.delay) - margin + tb <= base + ring_n]
+    starts += [(0, 780000), (1, 851234)]   # blocks without a transmission of the code
+    assert any((st0 % ring_n) + tb > ring_n for _, st0 in starts)   # some blocks wrap around
+    trackers = {}
+    st = torch.cuda.current_stream()
+    out = torch.zeros(64 * 48, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    found = 0
+    for code, start in starts:
+        t = trackers.setdefault(0, FskTracker(s, code, tb, d_ring.data_ptr(), ring_n))
+        got, n = t.run(code, start, stream=st.cuda_stream)
+        blk = torch.from_numpy(np.ascontiguousarray(w.iq16[start:start + tb])).cuda()
+        s.run_codes_ptr(st.cuda_stream, blk.data_ptr(), tb, start, [code], out.data_ptr(), 64, cnt.data_ptr())
+        st.synchronize()
+        n_ref = int(cnt.item())
+        ref = out.cpu().numpy().view(FSK_DETECTION_DTYPE)[:n_ref]
+        assert n == n_ref and got.tobytes() == ref.tobytes(), (code, start)
+        found += n
+    assert found >= 2
