@@ -585,8 +585,9 @@ def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
     demod_tf = demod_samples * fsk_demod_flops_per_sample(T) / (demod_avg / 1e3) / 1e12
     corr_share = prof["corr_ms"] / total_ms
     demod_share = prof["demod_ms"] / total_ms
-    dom = ("k_fsk_corr (packed inverse N-point transform over a cluster of 16 blocks, corr^2, floor, argmax per "
-           "(window pair, code))", corr_units, fsk_corr_flops_per_cell(N), corr_avg, corr_tf, corr_share) \
+    dom = ("k_fsk_corr_a + k_fsk_corr_b (packed inverse N-point transform per (window pair, code) in two passes: "
+           "16 blocks of 2^13 points to an L2-sized scratch, then the 16-point transform across them, corr^2, "
+           "floor, argmax)", corr_units, fsk_corr_flops_per_cell(N), corr_avg, corr_tf, corr_share) \
         if corr_share >= demod_share else \
         ("k_fsk_demod (int16 conversion, LO mix, both composed filters by 4096-point overlap-save transforms, d, u)",
          demod_samples, fsk_demod_flops_per_sample(T), demod_avg, demod_tf, demod_share)
@@ -601,7 +602,7 @@ def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
         "roofline": {"bound": "alu", "achieved": dom[4], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": dom[4] / FP32_PEAK_TFLOPS,
                      "traffic": (fsk_ncu_traffic_per_cell() * corr_units
-                                 if dom[0].startswith("k_fsk_corr") and fsk_ncu_traffic_per_cell() else None),
+                                 if dom[0].startswith("k_fsk_corr_a") and fsk_ncu_traffic_per_cell() else None),
                      "kernel": dom[0],
                      "units_per_launch": dom[1], "flops_per_unit": dom[2], "avg_launch_ms": dom[3],
                      "kernel_share_of_step": dom[5],

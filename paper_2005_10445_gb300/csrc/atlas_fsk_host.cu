@@ -61,6 +61,10 @@ struct atlas_fsk_ctx {
   int cand_cap = 0;
   int* d_ncand = nullptr;
   double* d_stats_part = nullptr;
+  // two-pass exchange of the cluster-sized transforms
+  int exchange = 0;               // 1: cluster, 2: two passes
+  float2* d_scratch = nullptr;
+  size_t scratch_elems = 0;
   // code selection of atlas_fsk_run_codes: per group, the group-local indices
   // then the global ids of the searched codes (pinned host staging, device copy)
   int* h_sel = nullptr;
@@ -120,6 +124,7 @@ void free_ctx(atlas_fsk_ctx* ctx) {
   cudaFree(ctx->d_cand);
   cudaFree(ctx->d_ncand);
   cudaFree(ctx->d_stats_part);
+  cudaFree(ctx->d_scratch);
   cudaFreeHost(ctx->h_sel);
   cudaFree(ctx->d_sel);
   if (ctx->ev_sel) cudaEventDestroy(ctx->ev_sel);
@@ -173,6 +178,15 @@ std::vector<float2> filter_spectrum(const std::vector<cd>& g, int B) {
   return out;
 }
 
+// (pair, code) items per pass of the two-pass exchange: about 64 MiB of scratch,
+// at most one launch group's items.
+int fsk_chunk_items(const atlas_fsk_ctx* ctx, const FskGroup& g) {
+  const int64_t per = (int64_t)g.N * (int64_t)sizeof(float2);
+  const int64_t by_size = std::max<int64_t>(1, (64ll << 20) / per);
+  const int64_t group = (int64_t)((ctx->wc + 1) / 2) * (int64_t)g.codes.size();
+  return (int)std::min(by_size, group);
+}
+
 int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_per_code, int32_t n_codes,
                 int32_t sps, double fs_hz, double f1_hz, double f0_hz, double f_lo_hz, const double* h_bp,
                 int32_t n_bp, const atlas_fsk_opts& o) {
@@ -185,7 +199,8 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   ctx->T = n_bp + sps - 1;
   ctx->threshold = o.threshold;
   if (ctx->T > atlas::kFskMaxTaps) return ATLAS_ERR_UNSUPPORTED;
-  if (o.windows_per_launch < 0) return ATLAS_ERR_INVALID_ARG;
+  if (o.windows_per_launch < 0 || o.exchange < 0 || o.exchange > 2) return ATLAS_ERR_INVALID_ARG;
+  ctx->exchange = o.exchange == 0 ? 2 : o.exchange;
   if (o.fft_len != 0 && (o.fft_len < (1 << atlas::kFskMinLogN) || o.fft_len > (1 << atlas::kFskMaxLogN) ||
                          (o.fft_len & (o.fft_len - 1)) != 0))
     return ATLAS_ERR_UNSUPPORTED;
@@ -351,6 +366,14 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   }
   ctx->buf_len = buf;
   ctx->cand_cap = cand;
+  if (ctx->exchange == 2) {  // scratch of one chunk of (pair, code) items, about 64 MiB
+    for (auto& g : ctx->groups)
+      if (g.R > 1)
+        ctx->scratch_elems = std::max(ctx->scratch_elems, (size_t)fsk_chunk_items(ctx, g) * g.N);
+    if (ctx->scratch_elems &&
+        cudaMalloc((void**)&ctx->d_scratch, sizeof(float2) * ctx->scratch_elems) != cudaSuccess)
+      return ATLAS_ERR_NO_MEMORY;
+  }
   if (cudaMalloc((void**)&ctx->d_dbuf, sizeof(float) * buf) != cudaSuccess ||
       cudaMalloc((void**)&ctx->d_ubuf, sizeof(float) * buf) != cudaSuccess ||
       cudaMalloc((void**)&ctx->d_X, sizeof(float2) * X_elems) != cudaSuccess ||
@@ -439,6 +462,10 @@ int enqueue_group(atlas_fsk_ctx* ctx, cudaStream_t st, const FskGroup& g, int W,
   cp.nw = nw;
   cp.Cg = Cg;
   cp.sel = d_sel_local;
+  if (ctx->exchange == 2 && g.R > 1) {
+    cp.scratch = ctx->d_scratch;
+    cp.chunk_items = fsk_chunk_items(ctx, g);
+  }
   const bool tc = timed && ctx->profiling && 2 * ctx->corr_used + 1 < (int)ctx->ev_corr.size();
   if (tc) CK(cudaEventRecord(ctx->ev_corr[2 * ctx->corr_used], st));
   CK(atlas::launch_fsk_corr(g.logN, cp, st));

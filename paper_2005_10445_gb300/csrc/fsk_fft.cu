@@ -28,6 +28,7 @@
 // code spectra conj(DFT(d_c)) / N, the inverse transform of X * C gives
 // corr_w + j corr_{w+1}.
 #include <cooperative_groups.h>
+#include <algorithm>
 #include <limits.h>
 
 #include "acq_common.cuh"
@@ -191,6 +192,81 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) 
   }
 }
 
+// Two-pass form of k_fsk_corr for R > 1: the same index maps with the
+// exchange through a scratch buffer in global memory (sized to stay in L2)
+// instead of distributed shared memory, so no block waits on another.
+//   pass A: block (item, r) inverse-transforms its run Z_perm[r M + .] and
+//           writes W_N^{-m r} Y_r[m] to scratch[(item - item0) R + r][m]
+//   pass B: block (item, rho) reads, for each m of its range, the R values
+//           scratch[.. r][m], takes the R-point DFT and the epilogue; its
+//           partial results are those of cluster block rho.
+// The values are the cluster form's, so the results are bit-identical.
+template <int LOGM, int R>
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) k_fsk_corr_a(FskCorrParams p,
+                                                                                           int item0) {
+  using FFT = BlockFFT<LOGM, kLogE, +1>;
+  constexpr int M = 1 << LOGM;
+  constexpr int N = M * R;
+  constexpr int LOGN = LOGM + ct_log2(R);
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  float2* sm_twN = sm_tw + TwTables<LOGM>::N;
+  load_tables<LOGM>(sm_tw, p.tw);
+  load_tables<LOGN>(sm_twN, p.twN);
+  const int local = blockIdx.x / R;
+  const int rank = blockIdx.x % R;
+  const int item = item0 + local;
+  const int pr = item / p.Cg, c = item % p.Cg;
+  const float2* X = p.X + (int64_t)pr * N + (int64_t)rank * M;
+  const float2* C = p.C + (int64_t)(p.sel ? p.sel[c] : c) * N + (int64_t)rank * M;
+  float2* out = p.scratch + ((int64_t)local * R + rank) * M;
+  auto load = [&](int k) { return cmul(X[k], C[k]); };
+  auto emit = [&](int m, float2 v) { out[m] = cmul(v, twiddle<LOGN, +1>(sm_twN, m * rank)); };
+  __syncthreads();  // tables
+  FFT::run(sm, sm_tw, load, emit);
+}
+
+template <int LOGM, int R>
+__global__ void __launch_bounds__(256) k_fsk_corr_b(FskCorrParams p, int item0) {
+  constexpr int M = 1 << LOGM;
+  constexpr int MR = M / R;
+  __shared__ float4 red[64];
+  const int local = blockIdx.x / R;
+  const int rank = blockIdx.x % R;
+  const int item = item0 + local;
+  const int pr = item / p.Cg, c = item % p.Cg;
+  const int wl0 = 2 * pr, wl1 = 2 * pr + 1;
+  const bool has1 = wl1 < p.nw;
+  const int nv0 = fsk_valid_lags(p, p.w0 + wl0);
+  const int nv1 = has1 ? fsk_valid_lags(p, p.w0 + wl1) : 0;
+  const float2* src = p.scratch + (int64_t)local * R * M;
+  float s0 = 0.f, b0 = -1.f, s1 = 0.f, b1 = -1.f;
+  int t0 = INT_MAX, t1 = INT_MAX;
+  for (int j = threadIdx.x; j < MR; j += blockDim.x) {
+    const int m = rank * MR + j;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(int64_t)r * M + m];
+    dft_reg<R, +1>(v);
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) {
+      const int tau = m + M * n2;
+      const float P0 = v[n2].x * v[n2].x, P1 = v[n2].y * v[n2].y;
+      s0 += P0;
+      s1 += P1;
+      if (tau < nv0) better(b0, t0, P0, tau);
+      if (tau < nv1) better(b1, t1, P1, tau);
+    }
+  }
+  block_reduce_stats(s0, b0, t0, red);
+  block_reduce_stats(s1, b1, t1, red + 32);
+  if (threadIdx.x == 0) {
+    p.part[((int64_t)wl0 * p.Cg + c) * R + rank] = make_float4(s0, b0, __int_as_float(t0), 0.f);
+    if (has1) p.part[((int64_t)wl1 * p.Cg + c) * R + rank] = make_float4(s1, b1, __int_as_float(t1), 0.f);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -206,6 +282,11 @@ cudaError_t prepare_one() {
   if ((e = cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)fsk_fft_smem<LOGM, LOGN>())) != cudaSuccess)
     return e;
+  if constexpr (R > 1) {
+    if ((e = cudaFuncSetAttribute(k_fsk_corr_a<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fsk_fft_smem<LOGM, LOGN>())) != cudaSuccess)
+      return e;
+  }
   if constexpr (R > 8) {  // clusters of 16 blocks are beyond the portable size
     if ((e = cudaFuncSetAttribute(k_fsk_fwd<LOGM, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
         cudaSuccess)
@@ -244,6 +325,20 @@ template <int LOGM, int R>
 cudaError_t corr_one(const FskCorrParams& p, cudaStream_t s) {
   constexpr int LOGN = LOGM + ct_log2(R);
   const int items = ((p.nw + 1) / 2) * p.Cg;
+  if constexpr (R > 1) {
+    if (p.scratch) {
+      if (p.chunk_items < 1) return cudaErrorInvalidValue;
+      for (int i0 = 0; i0 < items; i0 += p.chunk_items) {
+        const int n = std::min(p.chunk_items, items - i0);
+        k_fsk_corr_a<LOGM, R><<<n * R, fsk_fft_threads<LOGM>(), fsk_fft_smem<LOGM, LOGN>(), s>>>(p, i0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_fsk_corr_b<LOGM, R><<<n * R, 256, 0, s>>>(p, i0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+  }
   return launch_clustered(k_fsk_corr<LOGM, R>, R, items * R, fsk_fft_threads<LOGM>(), fsk_fft_smem<LOGM, LOGN>(),
                           p, s);
 }

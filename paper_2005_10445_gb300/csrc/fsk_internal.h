@@ -87,6 +87,11 @@ struct FskCorrParams {
   int N, hop, W, n_c;
   int w0, nw, Cg;
   const int* sel = nullptr;     // optional [Cg] group-local indices of the searched codes
+  // Two-pass form of the exchange (no cluster): scratch of chunk_items items
+  // x N values that holds the blocks' twiddled inverse transforms between the
+  // passes; null selects the cluster form.
+  float2* scratch = nullptr;
+  int chunk_items = 0;
 };
 
 // Per candidate of a launch group: the direct FP64 sums at the peak and the
