@@ -60,6 +60,16 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def fsk_kernel_source_hash() -> str:
+    """sha256 (first 16 hex digits) of the FSK correlation's kernel sources and
+    of the host file that sizes its passes."""
+    h = hashlib.sha256()
+    for f in ("fsk_fft.cu", "acq_common.cuh", "fft_block.cuh", "atlas_fsk_host.cu"):
+        with open(os.path.join(ROOT, "paper_2005_10445_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def fsk_ncu_traffic_per_cell():
     """DRAM bytes per (window, code) cell of k_fsk_corr from the committed ncu
     summary, if it was taken on the current kernel source."""
@@ -71,11 +81,7 @@ def fsk_ncu_traffic_per_cell():
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    h = hashlib.sha256()
-    for f in ("fsk_fft.cu", "acq_common.cuh", "fft_block.cuh"):
-        with open(os.path.join(ROOT, "paper_2005_10445_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+    if vals.get("kernel_source_sha256_16") != fsk_kernel_source_hash():
         return None
     try:
         return float(vals["dram_bytes_per_cell"])
@@ -586,7 +592,7 @@ def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
     corr_share = prof["corr_ms"] / total_ms
     demod_share = prof["demod_ms"] / total_ms
     dom = ("k_fsk_corr_a + k_fsk_corr_b (packed inverse N-point transform per (window pair, code) in two passes: "
-           "16 blocks of 2^13 points to an L2-sized scratch, then the 16-point transform across them, corr^2, "
+           "16 blocks of 2^13 points to a device scratch, then the 16-point transform across them, corr^2, "
            "floor, argmax)", corr_units, fsk_corr_flops_per_cell(N), corr_avg, corr_tf, corr_share) \
         if corr_share >= demod_share else \
         ("k_fsk_demod (int16 conversion, LO mix, both composed filters by 4096-point overlap-save transforms, d, u)",

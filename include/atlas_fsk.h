@@ -61,7 +61,7 @@ typedef struct {
   int32_t fft_len;            /* N for every code; 0 = 2 * nextpow2(L_c) per code */
   int32_t windows_per_launch; /* windows per launch group, rounded up to an even count; 0 = 64 */
   int32_t exchange;           /* transforms of more than 2^14 points: 0 = default (two passes
-                                 through an L2-sized scratch), 1 = one pass over a thread-block
+                                 through a device scratch of up to 1 GiB), 1 = one pass over a thread-block
                                  cluster exchanging through distributed shared memory, 2 = two
                                  passes; every form gives bit-identical results */
   int32_t reserved[4];

@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) 
 }
 
 // Two-pass form of k_fsk_corr for R > 1: the same index maps with the
-// exchange through a scratch buffer in global memory (sized to stay in L2)
-// instead of distributed shared memory, so no block waits on another.
+// exchange through a scratch buffer in global memory instead of distributed
+// shared memory, so no block waits on another.
 //   pass A: block (item, r) inverse-transforms its run Z_perm[r M + .] and
 //           writes W_N^{-m r} Y_r[m] to scratch[(item - item0) R + r][m]
 //   pass B: block (item, rho) reads, for each m of its range, the R values

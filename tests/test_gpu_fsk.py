@@ -259,8 +259,8 @@ def test_fsk_saturated_samples_and_zero_capacity(torch_cuda):
 @pytest.mark.parametrize("n_chips", [2048, 4096, 8192])
 def test_exchange_forms_are_bit_identical(torch_cuda, n_chips):
     """Transforms of 2^15-2^17 points: the cluster form (distributed shared
-    memory) and the two-pass form (L2-sized scratch, several chunks per launch
-    at 2^17) take the same values through the same arithmetic."""
+    memory) and the two-pass form (device scratch) take the same values
+    through the same arithmetic."""
     w = synth.fsk_realistic(seed=50 + n_chips, seconds=(6.3 * 2 * n_chips * 8) / 8e6, n_codes=12,
                             n_chips=n_chips, n_tags=4, snr_range=(-12.0, -3.0))
     _, a, na = gpu_run(torch_cuda, w, exchange=1)
