@@ -21,7 +21,7 @@
  *   8. j = argmax over the window's valid lags of |corr| (smallest on ties);
  *      score = corr[j]^2 / mean_{tau<N} corr[tau]^2; a detection when
  *      score >= threshold, with w_c = sum d_c[n] d[a+n], q = sum d[a+n]^2,
- *      p_c = sum d_c[n] u[a+n] (n < n_c, a = w hop + j, direct FP64 sums) and
+ *      p_c = sum d_c[n] u[a+n] (n < n_c, a = w hop + j, direct sums) and
  *      the arrival time a + delta, delta the vertex of the parabola through
  *      corr^2 at a-1, a, a+1 (0 at the stream ends).
  *
@@ -51,7 +51,8 @@ typedef struct {
   int32_t lag;     /* window-relative lag j; absolute lag a = window * hop_c + lag */
   float   score;   /* corr[j]^2 / floor (FP32 transform path) */
   double  toa;     /* a + delta, samples from the stream start */
-  double  w_c;     /* sum_n d_c[n] d[a+n]  (FP64 sums of the FP32 d, u, d_c) */
+  double  w_c;     /* sum_n d_c[n] d[a+n]  (direct sums of the FP32 d, u, d_c: FP32 over at most 9
+                      terms per thread, FP64 beyond) */
   double  q;       /* sum_n d[a+n]^2 */
   double  p_c;     /* sum_n d_c[n] u[a+n] */
 } atlas_fsk_detection;

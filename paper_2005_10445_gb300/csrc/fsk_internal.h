@@ -94,7 +94,8 @@ struct FskCorrParams {
   int chunk_items = 0;
 };
 
-// Per candidate of a launch group: the direct FP64 sums at the peak and the
+// Per candidate of a launch group: the direct sums at the peak (FP32 within a
+// thread's few terms, FP64 beyond) and the
 // parabolic arrival time (step 8); appends to the caller's list.
 struct FskStatsParams {
   const atlas_detection* cand;  // group's candidates (k_select output)

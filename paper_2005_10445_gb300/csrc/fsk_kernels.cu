@@ -9,8 +9,9 @@
 //   k_fsk_replica  step 6: the continuous-phase FSK replica of each code
 //   k_fsk_stats_part / _final
 //                  step 8 per candidate: w_c, q, p_c and the three
-//                  correlation values around the peak as direct FP64 sums (in
-//                  32 slices of the support, summed in order), the parabolic
+//                  correlation values around the peak as direct sums over the
+//                  support (32 slices; FP32 within a thread's few terms, FP64
+//                  across threads and slices, in a fixed order), the parabolic
 //                  arrival time, the record appended to the caller's list
 //   k_fsk_select   per (window, code): combines the cluster's partial results,
 //                  score, threshold, ordered compaction by a block prefix sum
@@ -122,8 +123,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int kFskStatsThreads = 256;
 
-// Stage 1: candidate b's five sums over slice s of n (n in [s*chunk, (s+1)*chunk)),
-// FP64 accumulation of exact FP32 products; persistent over (candidate, slice).
+// Stage 1: candidate b's five sums over slice s of n (n in [s*chunk, (s+1)*chunk));
+// persistent over (candidate, slice).
 __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_part(FskStatsParams p) {
   __shared__ double red[5][kFskStatsThreads / 32];
   const int n_items = *p.n_cand * kFskStatsSlices;
@@ -134,28 +135,30 @@ __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_part(FskStatsPar
     const atlas_detection cd = p.cand[b];
     const int64_t a = (int64_t)cd.window * p.hop + cd.lag;
     const float* dc = p.dc + (int64_t)cd.code * p.ld;
-    auto dv = [&](int64_t i) -> double {
+    auto dv = [&](int64_t i) -> float {
       const int64_t k = i - p.base;
-      return (k >= 0 && k < p.len) ? (double)p.d[k] : 0.0;
+      return (k >= 0 && k < p.len) ? p.d[k] : 0.f;
     };
-    double cm = 0.0, c0 = 0.0, cp = 0.0, q = 0.0, pc = 0.0;
+    // each thread sums its few terms (a slice of chunk <= 2100 over 256 threads)
+    // in FP32; the partial sums are combined in FP64
+    float fm = 0.f, f0 = 0.f, fp = 0.f, fq = 0.f, fu = 0.f;
     const int n1 = min(p.n_c, (sl + 1) * chunk);
     for (int n = sl * chunk + threadIdx.x; n < n1; n += blockDim.x) {
-      const double g = dc[n];  // products of two FP32 values are exact in FP64
-      const double d0 = dv(a + n);
+      const float g = dc[n];
+      const float d0 = dv(a + n);
       const int64_t k = a + n - p.base;
-      const double u0 = (k >= 0 && k < p.len) ? (double)p.u[k] : 0.0;
-      cm = fma(g, dv(a - 1 + n), cm);
-      c0 = fma(g, d0, c0);
-      cp = fma(g, dv(a + 1 + n), cp);
-      q = fma(d0, d0, q);
-      pc = fma(g, u0, pc);
+      const float u0 = (k >= 0 && k < p.len) ? p.u[k] : 0.f;
+      fm = fmaf(g, dv(a - 1 + n), fm);
+      f0 = fmaf(g, d0, f0);
+      fp = fmaf(g, dv(a + 1 + n), fp);
+      fq = fmaf(d0, d0, fq);
+      fu = fmaf(g, u0, fu);
     }
-    cm = warp_sum(cm);
-    c0 = warp_sum(c0);
-    cp = warp_sum(cp);
-    q = warp_sum(q);
-    pc = warp_sum(pc);
+    double cm = warp_sum((double)fm);
+    double c0 = warp_sum((double)f0);
+    double cp = warp_sum((double)fp);
+    double q = warp_sum((double)fq);
+    double pc = warp_sum((double)fu);
     __syncthreads();  // the previous item's reduction has been read
     if (lane == 0) {
       red[0][warp] = cm;
