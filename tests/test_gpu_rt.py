@@ -155,3 +155,49 @@ def test_tracker_single_launch_equals_block_search(torch_cuda):
         assert n == n_ref and got.tobytes() == ref.tobytes(), (code, start)
         found += n
     assert found >= 2
+
+
+def test_code_subsets_across_length_groups(torch_cuda):
+    """atlas_fsk_run_codes with a subset spanning two code-length groups (and a
+    continuing LO phase) reports exactly the full search's records of those
+    codes; an empty list reports nothing."""
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import FSK_DETECTION_DTYPE, FskSearch
+    w = synth.fsk_realistic(seed=61, seconds=0.04, chip_lengths=[1024, 2048, 1024, 2048, 1024], sps=8,
+                            n_tags=6, snr_range=(-8.0, -2.0))
+    s = FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp)
+    iq = torch.from_numpy(np.ascontiguousarray(w.iq16)).cuda()
+    full, n_full = s.run(iq)
+    assert n_full >= 3
+    st = torch.cuda.current_stream()
+    out = torch.zeros(256 * 48, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for subset in ([4, 1], [0, 3], [2], []):
+        s.run_codes_ptr(st.cuda_stream, iq.data_ptr(), w.n_samples, 0, subset, out.data_ptr(), 256, cnt.data_ptr())
+        st.synchronize()
+        n = int(cnt.item())
+        got = out.cpu().numpy().view(FSK_DETECTION_DTYPE)[:n]
+        want = full[np.isin(full["code"], subset)]
+        assert n == len(want) and got.tobytes() == want.tobytes(), subset
+
+
+def test_runtime_codes_of_two_lengths(torch_cuda):
+    """Tags of two code lengths: each length gets its own tracking graph; every
+    code is found by a searching task and then tracked without a miss."""
+    from paper_2005_10445_gb300 import binding as b
+    # each stream carries its own noise, so the sum has 3 dB more: the tags are stronger
+    w, periods = synth.fsk_periodic(seed=12, seconds=0.6, n_codes=4, n_chips=1024, snr_range=(-2.0, 1.0))
+    w2, periods2 = synth.fsk_periodic(seed=13, seconds=0.6, n_codes=2, n_chips=512, snr_range=(0.0, 3.0))
+    # one stream holding both sets of tags: the second set's samples added to the first's
+    x = w.iq16.astype(np.int32) + w2.iq16.astype(np.int32)
+    merged = w.__class__(**{**w.__dict__, "iq16": np.clip(x, -32768, 32767).astype(np.int16),
+                            "chips": list(w.chips) + list(w2.chips),
+                            "tags": list(w.tags) + [t.__class__(**{**t.__dict__, "code": t.code + 4})
+                                                    for t in w2.tags]})
+    rt, o = make_rt(merged, list(periods) + list(periods2))
+    ev = feed(rt, merged, 160000)
+    assert not np.any(np.isin(ev["kind"], [b.RT_TRACK_MISS, b.RT_TRACK_LOST]))
+    for c in range(6):
+        mine = ev[ev["code"] == c]
+        assert np.sum(mine["kind"] == b.RT_SEARCH_DETECTION) >= 1
+        assert np.sum(mine["kind"] == b.RT_TRACK_DETECTION) >= 2, c
