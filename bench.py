@@ -449,9 +449,10 @@ def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
         print(json.dumps(line), flush=True)
 
 
-FSK_WORKLOAD = ("fsk: 1 s of int16 (I, Q) at 8 MS/s (sigma 2048), 16 codes x 8192 chips at 8 samples/chip on "
-                "tones +/-500 kHz, band centre 1 MHz off the receiver's, 200-tap band-pass filter (T = 207), "
-                "N = 131072 (n_c = 65742, hop 65330, 122 windows), 40 tags at U[-15, 0] dB")
+def fsk_workload_name(N: int, hop: int, W: int) -> str:
+    return ("fsk: 1 s of int16 (I, Q) at 8 MS/s (sigma 2048), 16 codes x 8192 chips at 8 samples/chip on "
+            "tones +/-500 kHz, band centre 1 MHz off the receiver's, 200-tap band-pass filter (T = 207), "
+            f"N = {N} (n_c = 65742, hop {hop}, {W} windows), 40 tags at U[-15, 0] dB")
 
 
 def fsk_corr_flops_per_cell(N: int) -> float:
@@ -477,9 +478,9 @@ def fsk_oracle_sample(w, window: int = 1):
     """Time the FP64 oracle on one window x every code: (seconds, equivalent
     samples = hop)."""
     from oracle import fsk
-    N, W, hop, n_c = fsk.plan(w.n_samples, len(w.chips[0]), w.sps, len(w.h_bp) + w.sps - 1)
+    N, W, hop, n_c = fsk.plan(w.n_samples, len(w.chips[0]), w.sps, len(w.h_bp) + w.sps - 1, w.fft_len)
     t0 = time.perf_counter()
-    fsk.search(w.iq16, w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp,
+    fsk.search(w.iq16, w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp, w.fft_len,
                pairs=[(window, c) for c in range(len(w.chips))])
     return time.perf_counter() - t0, hop
 
@@ -491,7 +492,8 @@ def fsk_codes_in_real_time(args, w, iq, st, flush, dev, torch, n_codes: int = 12
     stream's tags use 16 of them) on the same resident 1-s stream."""
     from paper_2005_10445_gb300 import binding, synth
     chips = [synth.random_chips(8192, 2 * 1_000_003 + c) for c in range(n_codes)]
-    s = binding.FskSearch(chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp)
+    s = binding.FskSearch(chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp, fft_len=w.fft_len,
+                          block_log2=args.fsk_block_log2)
     S = w.n_samples
     cap = 4096
     out = torch.empty(cap * binding.FSK_DETECTION_DTYPE.itemsize, dtype=torch.uint8, device=dev)
@@ -521,10 +523,13 @@ def fsk_codes_in_real_time(args, w, iq, st, flush, dev, torch, n_codes: int = 12
 def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
     """The FSK front end (Section 3 steps 1-8) on 1 s of int16 samples."""
     from paper_2005_10445_gb300 import binding, synth
-    w = synth.fsk_realistic(seed=2 + rank)
+    w = synth.fsk_realistic(seed=2 + rank, fft_len=args.fsk_fft_len)
     S = w.n_samples
-    s = binding.FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp)
+    s = binding.FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp, fft_len=w.fft_len,
+                          block_log2=args.fsk_block_log2)
     Wn, hop, N, n_c = s.windows(0, S)
+    logN = N.bit_length() - 1
+    M = 1 << (args.fsk_block_log2 or (13 if logN <= 17 else 14)) if logN > 14 else N
     iq = torch.from_numpy(np.ascontiguousarray(w.iq16)).to(dev)
     cap = args.capacity
     rec = binding.FSK_DETECTION_DTYPE.itemsize
@@ -592,8 +597,8 @@ def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
     corr_share = prof["corr_ms"] / total_ms
     demod_share = prof["demod_ms"] / total_ms
     dom = ("k_fsk_corr_a + k_fsk_corr_b (packed inverse N-point transform per (window pair, code) in two passes: "
-           "16 blocks of 2^13 points to a device scratch, then the 16-point transform across them, corr^2, "
-           "floor, argmax)", corr_units, fsk_corr_flops_per_cell(N), corr_avg, corr_tf, corr_share) \
+           f"{N // M} blocks of {M} points to a device scratch, then the {N // M}-point transform across them, "
+           "corr^2, floor, argmax)", corr_units, fsk_corr_flops_per_cell(N), corr_avg, corr_tf, corr_share) \
         if corr_share >= demod_share else \
         ("k_fsk_demod (int16 conversion, LO mix, both composed filters by 4096-point overlap-save transforms, d, u)",
          demod_samples, fsk_demod_flops_per_sample(T), demod_avg, demod_tf, demod_share)
@@ -602,7 +607,8 @@ def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": FSK_WORKLOAD, "samples_per_step_per_gpu": S, "windows": Wn, "hop": hop,
+        "config": {"workload": fsk_workload_name(N, hop, Wn), "samples_per_step_per_gpu": S, "windows": Wn,
+                   "hop": hop, "fft_len": N, "block_points": M,
                    "l2": "flushed before each step (256 MiB write), outside the timed events",
                    "parallelism": "replicas: one independent stream per GPU", "detections_per_step": count},
         "roofline": {"bound": "alu", "achieved": dom[4], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -733,6 +739,9 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-unfused", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--capacity", type=int, default=4096)
+    ap.add_argument("--fsk-fft-len", type=int, default=1 << 18,
+                    help="FSK workload: N (0 = the library default, 2 nextpow2(L) = 2^17 here)")
+    ap.add_argument("--fsk-block-log2", type=int, default=0, help="FSK workload: log2 points per block (0 = default)")
     ap.add_argument("--workload", default="realistic", choices=["realistic", "batching", "learned", "precision", "fsk", "stream"])
     ap.add_argument("--train-windows", type=int, default=20000)
     ap.add_argument("--test-windows", type=int, default=2000)

@@ -65,7 +65,11 @@ typedef struct {
                                  through a device scratch of up to 1 GiB), 1 = one pass over a thread-block
                                  cluster exchanging through distributed shared memory, 2 = two
                                  passes; every form gives bit-identical results */
-  int32_t reserved[4];
+  int32_t block_log2;         /* transforms of more than 2^14 points: log2 of the points per block,
+                                 0 = default (13 up to N = 2^17, 14 at 2^18), 13 or 14 (N = 2^17
+                                 or 2^18 only); 32 blocks of 2^13 (N = 2^18) and blocks of 2^14 have
+                                 the two-pass form only */
+  int32_t reserved[3];
 } atlas_fsk_opts;
 
 void atlas_fsk_default_opts(atlas_fsk_opts* opts);
@@ -82,7 +86,7 @@ void atlas_fsk_default_opts(atlas_fsk_opts* opts);
  * Composes the filters in FP64 on the host, transforms them, builds every
  * code's replica, d_c and stored conjugated spectrum on the device (Section
  * 4.2: computed once and kept), allocates the workspaces and synchronises.
- * Supported: N a power of two, 2^10 .. 2^17, N > n_c; otherwise
+ * Supported: N a power of two, 2^10 .. 2^18, N > n_c; otherwise
  * ATLAS_ERR_UNSUPPORTED.  *out is released with atlas_fsk_destroy().
  */
 int atlas_fsk_create(atlas_fsk_t* out, const int8_t* chips, const int32_t* chips_per_code, int32_t n_codes,

@@ -85,7 +85,7 @@ class FskDetection(ctypes.Structure):
 class FskOpts(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_float), ("fft_len", ctypes.c_int32),
                 ("windows_per_launch", ctypes.c_int32), ("exchange", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("block_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class FskProfile(ctypes.Structure):
@@ -547,7 +547,7 @@ class FskSearch:
 
     def __init__(self, chips: Sequence[np.ndarray], samples_per_chip: int, fs_hz: float, f1_hz: float,
                  f0_hz: float, f_lo_hz: float, h_bp: np.ndarray, threshold: float = 49.0, fft_len: int = 0,
-                 windows_per_launch: int = 0, exchange: int = 0):
+                 windows_per_launch: int = 0, exchange: int = 0, block_log2: int = 0):
         lib = load()
         self._lib = lib
         self.ctx = ctypes.c_void_p()
@@ -563,6 +563,7 @@ class FskSearch:
         o.fft_len = fft_len
         o.windows_per_launch = windows_per_launch
         o.exchange = exchange
+        o.block_log2 = block_log2
         self.n_codes = len(chips)
         st = lib.atlas_fsk_create(ctypes.byref(self.ctx), cat.ctypes.data, cpc.ctypes.data, len(chips),
                                   samples_per_chip, float(fs_hz), float(f1_hz), float(f0_hz), float(f_lo_hz),

@@ -23,7 +23,7 @@ namespace {
 
 // Codes of one length share the window plan (n_c = L + T - 1, hop = N - n_c).
 struct FskGroup {
-  int n_chips = 0, L = 0, n_c = 0, N = 0, logN = 0, R = 1, hop = 0;
+  int n_chips = 0, L = 0, n_c = 0, N = 0, logN = 0, logM = 0, R = 1, hop = 0;
   std::vector<int> codes;
   int* d_codes = nullptr;      // [Cg] global code ids
   float2* d_spec = nullptr;    // [Cg][N] conj(DFT_N(d_c)) / N, permuted
@@ -202,7 +202,9 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   ctx->T = n_bp + sps - 1;
   ctx->threshold = o.threshold;
   if (ctx->T > atlas::kFskMaxTaps) return ATLAS_ERR_UNSUPPORTED;
-  if (o.windows_per_launch < 0 || o.exchange < 0 || o.exchange > 2) return ATLAS_ERR_INVALID_ARG;
+  if (o.windows_per_launch < 0 || o.exchange < 0 || o.exchange > 2 ||
+      (o.block_log2 != 0 && o.block_log2 != 13 && o.block_log2 != 14))
+    return ATLAS_ERR_INVALID_ARG;
   ctx->exchange = o.exchange == 0 ? 2 : o.exchange;
   if (o.fft_len != 0 && (o.fft_len < (1 << atlas::kFskMinLogN) || o.fft_len > (1 << atlas::kFskMaxLogN) ||
                          (o.fft_len & (o.fft_len - 1)) != 0))
@@ -226,7 +228,10 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
       g.N = o.fft_len ? o.fft_len : 2 * (int)(1ll << ilog2_ceil(g.L));
       g.logN = ilog2_ceil(g.N);
       if (g.logN < atlas::kFskMinLogN || g.logN > atlas::kFskMaxLogN || g.N <= g.n_c) return ATLAS_ERR_UNSUPPORTED;
-      g.R = g.logN > atlas::kFskLogMBlock ? 1 << (g.logN - atlas::kFskLogMCluster) : 1;
+      g.logM = g.logN > atlas::kFskLogMBlock && o.block_log2 ? o.block_log2 : atlas::fsk_default_log_m(g.logN);
+      if (!atlas::fsk_plan_supported(g.logN, g.logM)) return ATLAS_ERR_UNSUPPORTED;
+      g.R = 1 << (g.logN - g.logM);
+      if (ctx->exchange != 2 && !atlas::fsk_plan_has_cluster_form(g.logN, g.logM)) return ATLAS_ERR_UNSUPPORTED;
       g.hop = g.N - g.n_c;
       by_len[nch] = (int)ctx->groups.size();
       ctx->groups.push_back(g);
@@ -265,6 +270,22 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   const float2* twB = nullptr;
   int st = tables(atlas::kFskLogB, &twB);
   if (st != ATLAS_OK) return st;
+
+  // windows per launch group, an even count: windows are transformed in the
+  // pairs (2k, 2k + 1) of the whole stream whatever the grouping, so results
+  // do not depend on it
+  const int wpl = o.windows_per_launch > 0 ? o.windows_per_launch : 64;
+  ctx->wc = std::min((wpl + 1) / 2 * 2, 256);
+  // scratch of one pass of the two-pass transforms (also used by the code
+  // bank's forward transforms below)
+  if (ctx->exchange == 2) {
+    for (auto& g : ctx->groups)
+      if (g.R > 1)
+        ctx->scratch_elems = std::max(ctx->scratch_elems, (size_t)fsk_chunk_items(ctx, g) * g.N);
+    if (ctx->scratch_elems &&
+        cudaMalloc((void**)&ctx->d_scratch, sizeof(float2) * ctx->scratch_elems) != cudaSuccess)
+      return ATLAS_ERR_NO_MEMORY;
+  }
 
   // code bank: replica -> d_c -> conj(DFT_N(d_c)) / N (Section 3 step 6, kept: Section 4.2)
   int8_t* d_chips = nullptr;
@@ -340,7 +361,11 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
       fp.hop = 0;
       fp.w0 = 0;
       fp.nw = 0;
-      if (e == cudaSuccess) e = atlas::launch_fsk_fwd(g.logN, fp, 0);
+      if (ctx->exchange == 2 && g.R > 1) {
+        fp.scratch = ctx->d_scratch;
+        fp.chunk_items = (int)(ctx->scratch_elems / (size_t)g.N);
+      }
+      if (e == cudaSuccess) e = atlas::launch_fsk_fwd(g.logN, g.logM, fp, 0);
       if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
   }
@@ -353,11 +378,7 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
 
   // workspaces of one launch group: demodulated range, pair spectra, partial
   // results, candidates
-  // an even count: windows are transformed in the pairs (2k, 2k + 1) of the
-  // whole stream whatever the grouping, so results do not depend on it
-  int wc = o.windows_per_launch > 0 ? o.windows_per_launch : 64;
-  wc = std::min((wc + 1) / 2 * 2, 256);
-  ctx->wc = wc;
+  const int wc = ctx->wc;
   int64_t buf = 0;
   size_t X_elems = 0, part_elems = 0;
   int cand = 0;
@@ -369,14 +390,6 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   }
   ctx->buf_len = buf;
   ctx->cand_cap = cand;
-  if (ctx->exchange == 2) {  // scratch of one pass of (pair, code) items
-    for (auto& g : ctx->groups)
-      if (g.R > 1)
-        ctx->scratch_elems = std::max(ctx->scratch_elems, (size_t)fsk_chunk_items(ctx, g) * g.N);
-    if (ctx->scratch_elems &&
-        cudaMalloc((void**)&ctx->d_scratch, sizeof(float2) * ctx->scratch_elems) != cudaSuccess)
-      return ATLAS_ERR_NO_MEMORY;
-  }
   if (cudaMalloc((void**)&ctx->d_dbuf, sizeof(float) * buf) != cudaSuccess ||
       cudaMalloc((void**)&ctx->d_ubuf, sizeof(float) * buf) != cudaSuccess ||
       cudaMalloc((void**)&ctx->d_X, sizeof(float2) * X_elems) != cudaSuccess ||
@@ -449,7 +462,12 @@ int enqueue_group(atlas_fsk_ctx* ctx, cudaStream_t st, const FskGroup& g, int W,
   fp.X = ctx->d_X;
   fp.scale = 1.0f;
   fp.conj_out = 0;
-  CK(atlas::launch_fsk_fwd(g.logN, fp, st));
+  const bool two_pass = ctx->exchange == 2 && g.R > 1;
+  if (two_pass) {
+    fp.scratch = ctx->d_scratch;
+    fp.chunk_items = (int)(ctx->scratch_elems / (size_t)g.N);
+  }
+  CK(atlas::launch_fsk_fwd(g.logN, g.logM, fp, st));
   atlas::FskCorrParams cp;
   cp.X = ctx->d_X;
   cp.C = g.d_spec;
@@ -465,16 +483,21 @@ int enqueue_group(atlas_fsk_ctx* ctx, cudaStream_t st, const FskGroup& g, int W,
   cp.nw = nw;
   cp.Cg = Cg;
   cp.sel = d_sel_local;
-  if (ctx->exchange == 2 && g.R > 1) {
+  if (two_pass) {
     cp.scratch = ctx->d_scratch;
     cp.chunk_items = fsk_chunk_items(ctx, g);
   }
   const bool tc = timed && ctx->profiling && 2 * ctx->corr_used + 1 < (int)ctx->ev_corr.size();
   if (tc) CK(cudaEventRecord(ctx->ev_corr[2 * ctx->corr_used], st));
-  CK(atlas::launch_fsk_corr(g.logN, cp, st));
+  CK(atlas::launch_fsk_corr(g.logN, g.logM, cp, st));
   if (tc) CK(cudaEventRecord(ctx->ev_corr[2 * ctx->corr_used++ + 1], st));
   if (timed && ctx->profiling) {
-    ctx->prof.launches += 7;  // demod, forward, corr, select, two stats kernels, advance
+    // demod, select, two stats kernels, advance; the forward and the correlation
+    // transforms: one launch each, or two per pass of the two-pass form
+    const int fwd_items = fp.n_items, corr_items = ((nw + 1) / 2) * Cg;
+    auto passes = [](int items, int per) { return (items + per - 1) / per; };
+    ctx->prof.launches += 5 + (two_pass ? 2 * passes(fwd_items, fp.chunk_items) : 1) +
+                          (two_pass ? 2 * passes(corr_items, cp.chunk_items) : 1);
     ctx->prof.corr_launches += 1;
     ctx->prof.corr_units += (int64_t)nw * Cg;
     ctx->prof.demod_launches += 1;

@@ -1,10 +1,11 @@
 // fsk_fft.cu -- the N-point transforms of the FSK cross-correlation (Section 3
 // step 7, computed with FFTs as in Section 4.1).  N = R * M: M points live in
-// one block's shared memory (all of N up to 2^14 in one block; 2^13 per block
-// beyond) and R in {4, 8, 16} blocks of a thread-block cluster exchange through
-// distributed shared memory, so a transform of up to 2^17 points never goes
-// through global memory.  With 2^13 points (75 KB) per block three blocks fit
-// on an SM, and clusters of up to 16 blocks spread over every SM.
+// one block's shared memory (all of N up to 2^14 in one block; 2^13 or 2^14 per
+// block beyond) and R in {4, 8, 16} blocks exchange either through the
+// distributed shared memory of a thread-block cluster (M = 2^13, N up to 2^17:
+// 75 KB per block, three blocks per SM, clusters of up to 16 blocks spread
+// over every SM) or through a scratch buffer in global memory between two
+// passes (every plan, N up to 2^18).
 //
 // Index maps (n = m + M n2, k = R k2 + r with m, k2 < M and n2, r < R):
 //   forward   X[R k2 + r] = sum_m W_M^{m k2} ( W_N^{m r} sum_n2 x[m + M n2] W_R^{n2 r} )
@@ -40,12 +41,22 @@ namespace cg = cooperative_groups;
 template <int LOGM>
 constexpr int fsk_fft_threads() { return (1 << LOGM) >> kLogE; }
 
+// The tables of N sit in shared memory up to N = 2^17; beyond, blocks of 2^13
+// points read them through L1 so that three blocks still fit on an SM.
+template <int LOGN>
+constexpr bool fsk_twN_shared() { return LOGN <= 17; }
+
 // padded transform buffer, tables of M and of N, reduction scratch (2 x 32)
 template <int LOGM, int LOGN>
 constexpr size_t fsk_fft_smem() {
-  return sizeof(float2) * (BlockFFT<LOGM, kLogE, -1>::SMEM_ELEMS + TwTables<LOGM>::N + TwTables<LOGN>::N) +
+  return sizeof(float2) * (BlockFFT<LOGM, kLogE, -1>::SMEM_ELEMS + TwTables<LOGM>::N +
+                           (fsk_twN_shared<LOGN>() ? TwTables<LOGN>::N : 0)) +
          64 * sizeof(float4);
 }
+
+// clusters hold at most 16 blocks
+template <int LOGM, int R>
+constexpr bool fsk_cluster_form() { return R == 1 || (LOGM <= 13 && R <= 16); }
 
 // The passes of a block FFT whose input is already in shared memory (natural
 // index i at spad(i)).
@@ -70,12 +81,13 @@ __device__ __forceinline__ float fsk_fwd_value(const FskFwdParams& p, int item, 
   return (i >= 0 && i < p.len) ? p.d[i] : 0.f;
 }
 
-// blocks per SM the cluster kernels are compiled for (register budget)
-template <int R>
-constexpr int fsk_min_blocks() { return R > 1 ? 3 : 1; }
+// blocks per SM the multi-block kernels are compiled for (register budget):
+// three of 2^13 points, one of 2^14
+template <int LOGM, int R>
+constexpr int fsk_min_blocks() { return (R > 1 && LOGM <= 13) ? 3 : 1; }
 
 template <int LOGM, int R>
-__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) k_fsk_fwd(FskFwdParams p) {
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<LOGM, R>()) k_fsk_fwd(FskFwdParams p) {
   using FFT = BlockFFT<LOGM, kLogE, -1>;
   constexpr int M = 1 << LOGM;
   constexpr int N = M * R;
@@ -119,6 +131,65 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) 
   }
 }
 
+// Two-pass form of k_fsk_fwd for R > 1: the same index maps and arithmetic,
+// with the exchange through a scratch buffer in global memory instead of
+// distributed shared memory, so no block waits on another and a block may hold
+// 2^14 points (one per SM, more than a cluster of 16 can place at once).
+//   pass A: block (item, rho) takes the m of its range, forms the R-point DFT
+//           of the values x[m + M n2] and writes value r times W_N^{m r} to
+//           scratch[(item - item0) R + r][m]
+//   pass B: block (item, r) transforms scratch row r with the block FFT and
+//           writes the run X_perm[r M + .]
+// The first pass of the block FFT reads the same values the cluster form
+// reads from shared memory, so the results are bit-identical.
+template <int LOGM, int R>
+__global__ void __launch_bounds__(256) k_fsk_fwd_a(FskFwdParams p, int item0) {
+  constexpr int M = 1 << LOGM;
+  constexpr int N = M * R;
+  constexpr int LOGN = LOGM + ct_log2(R);
+  constexpr int MR = M / R;
+  __shared__ float2 sm_twN[TwTables<LOGN>::N];
+  load_tables<LOGN>(sm_twN, p.twN);
+  __syncthreads();
+  const int local = blockIdx.x / R;
+  const int rank = blockIdx.x % R;
+  const int item = item0 + local;
+  float2* dst = p.scratch + (int64_t)local * N;
+  for (int j = threadIdx.x; j < MR; j += blockDim.x) {
+    const int m = rank * MR + j;
+    float2 v[R];
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2)
+      v[n2] = make_float2(fsk_fwd_value(p, item, 0, m + M * n2), fsk_fwd_value(p, item, 1, m + M * n2));
+    dft_reg<R, -1>(v);
+    dst[m] = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) dst[(int64_t)r * M + m] = cmul(v[r], twiddle<LOGN, -1>(sm_twN, m * r));
+  }
+}
+
+template <int LOGM, int R>
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<LOGM, R>()) k_fsk_fwd_b(FskFwdParams p,
+                                                                                                 int item0) {
+  using FFT = BlockFFT<LOGM, kLogE, -1>;
+  constexpr int M = 1 << LOGM;
+  constexpr int N = M * R;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + FFT::SMEM_ELEMS;
+  load_tables<LOGM>(sm_tw, p.tw);
+  const int local = blockIdx.x / R;
+  const int rank = blockIdx.x % R;
+  const float2* src = p.scratch + ((int64_t)local * R + rank) * M;
+  float2* X = p.X + (int64_t)(item0 + local) * N + (int64_t)rank * M;
+  const float sc = p.scale;
+  const float sy = p.conj_out ? -sc : sc;
+  auto load = [&](int i) { return src[i]; };
+  auto emit = [&](int k, float2 v) { X[k] = make_float2(v.x * sc, v.y * sy); };
+  __syncthreads();  // tables
+  FFT::run(sm, sm_tw, load, emit);
+}
+
 // valid lags of window w (the overlap rule with the support n_c)
 __device__ __forceinline__ int fsk_valid_lags(const FskCorrParams& p, int w) {
   if (w < p.W - 1) return p.hop;
@@ -127,7 +198,7 @@ __device__ __forceinline__ int fsk_valid_lags(const FskCorrParams& p, int w) {
 }
 
 template <int LOGM, int R>
-__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) k_fsk_corr(FskCorrParams p) {
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<LOGM, R>()) k_fsk_corr(FskCorrParams p) {
   using FFT = BlockFFT<LOGM, kLogE, +1>;
   constexpr int M = 1 << LOGM;
   constexpr int N = M * R;
@@ -202,7 +273,7 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) 
 //           partial results are those of cluster block rho.
 // The values are the cluster form's, so the results are bit-identical.
 template <int LOGM, int R>
-__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) k_fsk_corr_a(FskCorrParams p,
+__global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<LOGM, R>()) k_fsk_corr_a(FskCorrParams p,
                                                                                            int item0) {
   using FFT = BlockFFT<LOGM, kLogE, +1>;
   constexpr int M = 1 << LOGM;
@@ -213,7 +284,8 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) 
   float2* sm_tw = sm + FFT::SMEM_ELEMS;
   float2* sm_twN = sm_tw + TwTables<LOGM>::N;
   load_tables<LOGM>(sm_tw, p.tw);
-  load_tables<LOGN>(sm_twN, p.twN);
+  if constexpr (fsk_twN_shared<LOGN>()) load_tables<LOGN>(sm_twN, p.twN);
+  const float2* twN = fsk_twN_shared<LOGN>() ? sm_twN : p.twN;
   const int local = blockIdx.x / R;
   const int rank = blockIdx.x % R;
   const int item = item0 + local;
@@ -222,7 +294,7 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<R>()) 
   const float2* C = p.C + (int64_t)(p.sel ? p.sel[c] : c) * N + (int64_t)rank * M;
   float2* out = p.scratch + ((int64_t)local * R + rank) * M;
   auto load = [&](int k) { return cmul(X[k], C[k]); };
-  auto emit = [&](int m, float2 v) { out[m] = cmul(v, twiddle<LOGN, +1>(sm_twN, m * rank)); };
+  auto emit = [&](int m, float2 v) { out[m] = cmul(v, twiddle<LOGN, +1>(twN, m * rank)); };
   __syncthreads();  // tables
   FFT::run(sm, sm_tw, load, emit);
 }
@@ -276,22 +348,31 @@ namespace {
 template <int LOGM, int R>
 cudaError_t prepare_one() {
   constexpr int LOGN = LOGM + ct_log2(R);
-  cudaError_t e = cudaFuncSetAttribute(k_fsk_fwd<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fsk_fft_smem<LOGM, LOGN>());
-  if (e != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fsk_fft_smem<LOGM, LOGN>())) != cudaSuccess)
-    return e;
-  if constexpr (R > 1) {
-    if ((e = cudaFuncSetAttribute(k_fsk_corr_a<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fsk_fft_smem<LOGM, LOGN>())) != cudaSuccess)
-      return e;
-  }
-  if constexpr (R > 8) {  // clusters of 16 blocks are beyond the portable size
-    if ((e = cudaFuncSetAttribute(k_fsk_fwd<LOGM, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+  constexpr int smem = (int)fsk_fft_smem<LOGM, LOGN>();
+  cudaError_t e;
+  if constexpr (fsk_cluster_form<LOGM, R>()) {  // the single-block and cluster forms
+    if ((e = cudaFuncSetAttribute(k_fsk_fwd<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
         cudaSuccess)
       return e;
-    return cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if ((e = cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+        cudaSuccess)
+      return e;
+    if constexpr (R > 8) {  // clusters of 16 blocks are beyond the portable size
+      if ((e = cudaFuncSetAttribute(k_fsk_fwd<LOGM, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+          cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(k_fsk_corr<LOGM, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+          cudaSuccess)
+        return e;
+    }
+  }
+  if constexpr (R > 1) {  // the two-pass forms
+    if ((e = cudaFuncSetAttribute(k_fsk_fwd_b<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_fsk_corr_a<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+        cudaSuccess)
+      return e;
   }
   return cudaSuccess;
 }
@@ -317,8 +398,26 @@ cudaError_t launch_clustered(void (*kern)(P), int R, int blocks, int threads, si
 template <int LOGM, int R>
 cudaError_t fwd_one(const FskFwdParams& p, cudaStream_t s) {
   constexpr int LOGN = LOGM + ct_log2(R);
-  return launch_clustered(k_fsk_fwd<LOGM, R>, R, p.n_items * R, fsk_fft_threads<LOGM>(),
-                          fsk_fft_smem<LOGM, LOGN>(), p, s);
+  if constexpr (R > 1) {
+    if (p.scratch) {
+      if (p.chunk_items < 1) return cudaErrorInvalidValue;
+      for (int i0 = 0; i0 < p.n_items; i0 += p.chunk_items) {
+        const int n = std::min(p.chunk_items, p.n_items - i0);
+        k_fsk_fwd_a<LOGM, R><<<n * R, 256, 0, s>>>(p, i0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_fsk_fwd_b<LOGM, R><<<n * R, fsk_fft_threads<LOGM>(), fsk_fft_smem<LOGM, LOGN>(), s>>>(p, i0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+  }
+  if constexpr (!fsk_cluster_form<LOGM, R>()) {
+    return cudaErrorInvalidValue;  // two-pass form only
+  } else {
+    return launch_clustered(k_fsk_fwd<LOGM, R>, R, p.n_items * R, fsk_fft_threads<LOGM>(),
+                            fsk_fft_smem<LOGM, LOGN>(), p, s);
+  }
 }
 
 template <int LOGM, int R>
@@ -339,8 +438,12 @@ cudaError_t corr_one(const FskCorrParams& p, cudaStream_t s) {
       return cudaSuccess;
     }
   }
-  return launch_clustered(k_fsk_corr<LOGM, R>, R, items * R, fsk_fft_threads<LOGM>(), fsk_fft_smem<LOGM, LOGN>(),
-                          p, s);
+  if constexpr (!fsk_cluster_form<LOGM, R>()) {
+    return cudaErrorInvalidValue;  // two-pass form only
+  } else {
+    return launch_clustered(k_fsk_corr<LOGM, R>, R, items * R, fsk_fft_threads<LOGM>(),
+                            fsk_fft_smem<LOGM, LOGN>(), p, s);
+  }
 }
 
 }  // namespace
@@ -354,11 +457,15 @@ cudaError_t fsk_prepare_fft() {
   if ((e = prepare_one<14, 1>()) != cudaSuccess) return e;
   if ((e = prepare_one<13, 4>()) != cudaSuccess) return e;
   if ((e = prepare_one<13, 8>()) != cudaSuccess) return e;
-  return prepare_one<13, 16>();
+  if ((e = prepare_one<13, 16>()) != cudaSuccess) return e;
+  if ((e = prepare_one<14, 8>()) != cudaSuccess) return e;
+  if ((e = prepare_one<13, 32>()) != cudaSuccess) return e;
+  return prepare_one<14, 16>();
 }
 
-cudaError_t launch_fsk_fwd(int logN, const FskFwdParams& p, cudaStream_t s) {
+cudaError_t launch_fsk_fwd(int logN, int logM, const FskFwdParams& p, cudaStream_t s) {
   if (p.n_items <= 0) return cudaSuccess;
+  if (!fsk_plan_supported(logN, logM)) return cudaErrorInvalidValue;
   switch (logN) {
     case 10: return fwd_one<10, 1>(p, s);
     case 11: return fwd_one<11, 1>(p, s);
@@ -367,13 +474,15 @@ cudaError_t launch_fsk_fwd(int logN, const FskFwdParams& p, cudaStream_t s) {
     case 14: return fwd_one<14, 1>(p, s);
     case 15: return fwd_one<13, 4>(p, s);
     case 16: return fwd_one<13, 8>(p, s);
-    case 17: return fwd_one<13, 16>(p, s);
+    case 17: return logM == 14 ? fwd_one<14, 8>(p, s) : fwd_one<13, 16>(p, s);
+    case 18: return logM == 14 ? fwd_one<14, 16>(p, s) : fwd_one<13, 32>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_fsk_corr(int logN, const FskCorrParams& p, cudaStream_t s) {
+cudaError_t launch_fsk_corr(int logN, int logM, const FskCorrParams& p, cudaStream_t s) {
   if (p.nw <= 0 || p.Cg <= 0) return cudaSuccess;
+  if (!fsk_plan_supported(logN, logM)) return cudaErrorInvalidValue;
   switch (logN) {
     case 10: return corr_one<10, 1>(p, s);
     case 11: return corr_one<11, 1>(p, s);
@@ -382,7 +491,8 @@ cudaError_t launch_fsk_corr(int logN, const FskCorrParams& p, cudaStream_t s) {
     case 14: return corr_one<14, 1>(p, s);
     case 15: return corr_one<13, 4>(p, s);
     case 16: return corr_one<13, 8>(p, s);
-    case 17: return corr_one<13, 16>(p, s);
+    case 17: return logM == 14 ? corr_one<14, 8>(p, s) : corr_one<13, 16>(p, s);
+    case 18: return logM == 14 ? corr_one<14, 16>(p, s) : corr_one<13, 32>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }

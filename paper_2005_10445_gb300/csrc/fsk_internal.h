@@ -15,9 +15,22 @@ namespace atlas {
 constexpr int kFskLogB = 12;          // demodulation block: 4096-point transforms
 constexpr int kFskMaxTaps = 1024;     // composed filter taps T (<= B / 4)
 constexpr int kFskMinLogN = 10;
-constexpr int kFskMaxLogN = 17;
+constexpr int kFskMaxLogN = 18;
 constexpr int kFskLogMBlock = 14;     // largest transform one block holds alone
-constexpr int kFskLogMCluster = 13;   // points per block when a transform spans a cluster
+
+// Points per block (log2) of a transform of 2^logN points: the whole transform
+// up to 2^14; beyond, 2^13 (three blocks per SM) up to 2^17 and 2^14 (one
+// block per SM) at 2^18.
+constexpr int fsk_default_log_m(int logN) { return logN <= kFskLogMBlock ? logN : (logN <= 17 ? 13 : 14); }
+// The (logN, logM) pairs with compiled kernels.  Plans of more than 16 blocks
+// or of blocks of 2^14 points have the two-pass form only.
+constexpr bool fsk_plan_supported(int logN, int logM) {
+  return logN <= kFskLogMBlock ? logM == logN
+                               : ((logM == 13 && logN <= 18) || (logM == 14 && (logN == 17 || logN == 18)));
+}
+constexpr bool fsk_plan_has_cluster_form(int logN, int logM) {
+  return logN <= kFskLogMBlock || (logM == 13 && logN <= 17);
+}
 constexpr int kFskStatsSlices = 32;   // slices of the support per candidate in the peak sums
 
 // Steps 1-5 over an index range of the stream (or of a replica): conversion,
@@ -72,6 +85,10 @@ struct FskFwdParams {
   float2* X;                    // out [n_items][N]
   float scale;                  // applied to the output
   int conj_out;                 // 1: write conj(X) * scale
+  // Two-pass form (R > 1): scratch of chunk_items items x N values between the
+  // R-point and the M-point stages; null selects the cluster form.
+  float2* scratch = nullptr;
+  int chunk_items = 0;
 };
 
 // Per (window pair, code): Z = X * C, inverse N-point transform, corr^2,
@@ -117,9 +134,9 @@ cudaError_t fsk_prepare_fft();  // (the transform kernels; called by fsk_prepare
 cudaError_t launch_fsk_demod(const FskDemodParams& p, cudaStream_t s);
 int64_t fsk_demod_outputs_per_block(int T);
 cudaError_t launch_fsk_replica(const FskReplicaParams& p, int n_codes, int L, cudaStream_t s);
-// logN in [kFskMinLogN, kFskMaxLogN]
-cudaError_t launch_fsk_fwd(int logN, const FskFwdParams& p, cudaStream_t s);
-cudaError_t launch_fsk_corr(int logN, const FskCorrParams& p, cudaStream_t s);
+// N = 2^logN points as 2^(logN - logM) blocks of 2^logM (fsk_plan_supported)
+cudaError_t launch_fsk_fwd(int logN, int logM, const FskFwdParams& p, cudaStream_t s);
+cudaError_t launch_fsk_corr(int logN, int logM, const FskCorrParams& p, cudaStream_t s);
 // selection of a launch group (SelectParams with K = 1, sps = R partials per cell)
 cudaError_t launch_fsk_select(const SelectParams& p, cudaStream_t s);
 cudaError_t launch_fsk_stats(const FskStatsParams& p, int max_cand, cudaStream_t s);

@@ -466,15 +466,17 @@ def fsk_small(seed: int = 11, S: int = 40000, n_codes: int = 3, n_chips: int = 6
 
 def fsk_realistic(seed: int = 2, seconds: float = 1.0, n_codes: int = 16, n_chips: int = 8192, sps: int = 8,
                   fs_hz: float = 8e6, f_lo_hz: float = 1e6, n_tags: int = 40, snr_range=(-15.0, 0.0),
-                  chip_lengths: Optional[Sequence[int]] = None) -> FskWorkload:
+                  chip_lengths: Optional[Sequence[int]] = None, fft_len: int = 0) -> FskWorkload:
     """1 s at 8 MS/s of int16 samples, 16 codes x 8192 chips at 8 samples/chip
     on tones +/-500 kHz around a band centre 1 MHz off the receiver's, a
     200-tap band-pass filter, 40 tags with SNR U[-15, 0] dB.  chip_lengths
-    (optional) gives each code its own length."""
+    (optional) gives each code its own length; fft_len (optional) the window
+    N, which also sets the smallest gap between transmissions of one code
+    (2 N)."""
     S = int(round(seconds * fs_hz))
     lens = list(chip_lengths) if chip_lengths is not None else [n_chips] * n_codes
     chips = [random_chips(n, seed * 1_000_003 + c) for c, n in enumerate(lens)]
-    return fsk_stream(seed, S, chips, sps, fs_hz, 5e5, -5e5, f_lo_hz, n_tags, snr_range,
+    return fsk_stream(seed, S, chips, sps, fs_hz, 5e5, -5e5, f_lo_hz, n_tags, snr_range, fft_len=fft_len,
                       name=f"fsk realistic: {S} samples at {fs_hz/1e6:g} MS/s, {len(chips)} codes, sps {sps}")
 
 

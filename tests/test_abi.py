@@ -122,6 +122,7 @@ def test_fsk_struct_sizes_and_defaults(lib):
     o = binding.FskOpts()
     lib.atlas_fsk_default_opts(ctypes.byref(o))
     assert o.threshold == 49.0 and o.fft_len == 0 and o.windows_per_launch == 0
+    assert o.exchange == 0 and o.block_log2 == 0
 
 
 def _fsk_create(lib, chips, cpc, n_codes, sps, fs, taps, n_bp, opts=None, f1=5e5, f0=-5e5, f_lo=0.0):
@@ -156,6 +157,9 @@ def test_fsk_create_rejects_bad_arguments(lib):
     lib.atlas_fsk_default_opts(ctypes.byref(o))
     o.threshold = -2.0
     assert _fsk_create(lib, ch, [1000], 1, 2, 2e6, taps, 200, o) == E
+    lib.atlas_fsk_default_opts(ctypes.byref(o))
+    o.block_log2 = 12                                                      # 13, 14 or 0 only
+    assert _fsk_create(lib, ch, [1000], 1, 2, 2e6, taps, 200, o) == E
 
 
 def test_fsk_create_rejects_unsupported_sizes(lib):
@@ -164,7 +168,7 @@ def test_fsk_create_rejects_unsupported_sizes(lib):
     taps = np.zeros((1100, 2))
     taps[:, 0] = 1e-3
     assert _fsk_create(lib, ch[:1000], [1000], 1, 2, 2e6, taps, 1100) == U     # T = 1101 taps > 1024
-    assert _fsk_create(lib, ch, [20000], 1, 8, 8e6, taps, 200) == U            # N = 2^19 > 2^17
+    assert _fsk_create(lib, ch, [20000], 1, 8, 8e6, taps, 200) == U            # N = 2^19 > 2^18
     o = binding.FskOpts()
     lib.atlas_fsk_default_opts(ctypes.byref(o))
     o.fft_len = 5000                                                          # not a power of two
@@ -172,6 +176,12 @@ def test_fsk_create_rejects_unsupported_sizes(lib):
     o.fft_len = 512                                                           # below 2^10
     assert _fsk_create(lib, ch[:100], [100], 1, 2, 2e6, taps, 20, o) == U
     o.fft_len = 2048                                                          # N <= n_c = 2000 + 200
+    assert _fsk_create(lib, ch[:1000], [1000], 1, 2, 2e6, taps, 200, o) == U
+    o.fft_len = 1 << 19                                                       # above 2^18
+    assert _fsk_create(lib, ch[:1000], [1000], 1, 2, 2e6, taps, 200, o) == U
+    o.fft_len, o.block_log2 = 1 << 16, 14                                     # 4 blocks of 2^14: no kernels
+    assert _fsk_create(lib, ch[:1000], [1000], 1, 2, 2e6, taps, 200, o) == U
+    o.fft_len, o.block_log2, o.exchange = 1 << 18, 0, 1                       # 2^14-point blocks: two passes only
     assert _fsk_create(lib, ch[:1000], [1000], 1, 2, 2e6, taps, 200, o) == U
 
 

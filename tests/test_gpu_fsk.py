@@ -133,8 +133,8 @@ def test_small_parity_and_tags(torch_cuda):
 
 @pytest.mark.parametrize("n_chips", [1024, 2048, 4096, 8192])
 def test_transform_sizes(torch_cuda, n_chips):
-    """N = 2^14 (one block), 2^15, 2^16, 2^17 (clusters of 2, 4 and 8 blocks);
-    about 2.7 windows of stream, ragged tail, two codes."""
+    """N = 2^14 (one block), 2^15, 2^16, 2^17 (4, 8 and 16 blocks of 2^13
+    points, two passes); about 2.7 windows of stream, ragged tail, two codes."""
     L = n_chips * 8
     S = int(2.7 * 2 * L) + 1234
     w = synth.fsk_realistic(seed=20 + n_chips, seconds=S / 8e6, n_codes=2, n_chips=n_chips, n_tags=3,
@@ -145,6 +145,37 @@ def test_transform_sizes(torch_cuda, n_chips):
     ora = oracle(w)
     assert n == len(ora) >= 1
     compare(dets, ora)
+
+
+@pytest.mark.parametrize("fft_len,block_log2,seconds", [(1 << 18, 0, 0.075), (1 << 18, 13, 0.075),
+                                                        (1 << 18, 14, 0.075), (1 << 17, 14, 0.045)])
+def test_two_pass_only_plans(torch_cuda, fft_len, block_log2, seconds):
+    """Plans with no cluster form: N = 2^18 as 32 blocks of 2^13 points or 16
+    of 2^14 (and the default there), N = 2^17 as 8 blocks of 2^14; about 2.7
+    windows of stream, ragged tail, two codes."""
+    w = synth.fsk_realistic(seed=23, seconds=seconds, n_codes=2, n_tags=3, snr_range=(-12.0, -3.0),
+                            fft_len=fft_len)
+    s, dets, n = gpu_run(torch_cuda, w, block_log2=block_log2)
+    Wn, hop, N, n_c = s.windows(0, w.n_samples)
+    assert N == fft_len and Wn >= 3
+    ora = oracle(w)
+    assert n == len(ora) >= 1
+    compare(dets, ora)
+
+
+def test_block_sizes_agree_at_2_17(torch_cuda):
+    """N = 2^17 as sixteen blocks of 2^13 points or eight of 2^14: different
+    factorisations of the same transform, the same detections with scores and
+    sums within FP32 rounding of each other."""
+    w = synth.fsk_realistic(seed=24, seconds=0.06, n_codes=4, n_tags=5, snr_range=(-12.0, -3.0))
+    _, a, na = gpu_run(torch_cuda, w, block_log2=13)
+    _, b, nb = gpu_run(torch_cuda, w, block_log2=14)
+    assert na == nb >= 1
+    assert [(int(d["code"]), int(d["window"]), int(d["lag"])) for d in a] == \
+        [(int(d["code"]), int(d["window"]), int(d["lag"])) for d in b]
+    for x, y in zip(a, b):
+        assert x["score"] == pytest.approx(y["score"], rel=SCORE_RTOL)
+        assert x["w_c"] == y["w_c"] and x["q"] == y["q"] and x["toa"] == y["toa"]
 
 
 def test_mixed_code_lengths(torch_cuda):
@@ -202,11 +233,12 @@ def test_stream_of_exactly_one_support(torch_cuda):
     compare(dets, ora)
 
 
-def test_realistic_full_size_sampled(torch_cuda):
-    """1 s at 8 MS/s, 16 codes x 8192 chips (N = 2^17, clusters of 8 blocks):
-    every injected tag found at its delay; the oracle recomputes the cells of
-    two detections and of one tag."""
-    w = synth.fsk_realistic()
+@pytest.mark.parametrize("fft_len", [0, 1 << 18])
+def test_realistic_full_size_sampled(torch_cuda, fft_len):
+    """1 s at 8 MS/s, 16 codes x 8192 chips (N = 2^17, sixteen blocks of 2^13
+    points; N = 2^18, sixteen blocks of 2^14): every injected tag found at its
+    delay; the oracle recomputes the cells of two detections and of one tag."""
+    w = synth.fsk_realistic(fft_len=fft_len)
     s, dets, n = gpu_run(torch_cuda, w)
     assert n == len(dets) >= len(w.tags)
     Wn, hop, N, n_c = s.windows(0, w.n_samples)
@@ -258,9 +290,9 @@ def test_fsk_saturated_samples_and_zero_capacity(torch_cuda):
 
 @pytest.mark.parametrize("n_chips", [2048, 4096, 8192])
 def test_exchange_forms_are_bit_identical(torch_cuda, n_chips):
-    """Transforms of 2^15-2^17 points: the cluster form (distributed shared
-    memory) and the two-pass form (device scratch) take the same values
-    through the same arithmetic."""
+    """Transforms of 2^15-2^17 points, forward and inverse: the cluster form
+    (distributed shared memory) and the two-pass form (device scratch) take
+    the same values through the same arithmetic."""
     w = synth.fsk_realistic(seed=50 + n_chips, seconds=(6.3 * 2 * n_chips * 8) / 8e6, n_codes=12,
                             n_chips=n_chips, n_tags=4, snr_range=(-12.0, -3.0))
     _, a, na = gpu_run(torch_cuda, w, exchange=1)
