@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<LOGM, 
   }
 }
 
+// The scratch of the two-pass forms is written and read once each with
+// streaming (evict-first) accesses, so that it does not push the window and
+// code spectra, which every block reads, out of L2.
+//
 // Two-pass form of k_fsk_fwd for R > 1: the same index maps and arithmetic,
 // with the exchange through a scratch buffer in global memory instead of
 // distributed shared memory, so no block waits on another and a block may hold
@@ -162,9 +166,9 @@ __global__ void __launch_bounds__(256) k_fsk_fwd_a(FskFwdParams p, int item0) {
     for (int n2 = 0; n2 < R; ++n2)
       v[n2] = make_float2(fsk_fwd_value(p, item, 0, m + M * n2), fsk_fwd_value(p, item, 1, m + M * n2));
     dft_reg<R, -1>(v);
-    dst[m] = v[0];
+    __stcs(dst + m, v[0]);
 #pragma unroll
-    for (int r = 1; r < R; ++r) dst[(int64_t)r * M + m] = cmul(v[r], twiddle<LOGN, -1>(sm_twN, m * r));
+    for (int r = 1; r < R; ++r) __stcs(dst + (int64_t)r * M + m, cmul(v[r], twiddle<LOGN, -1>(sm_twN, m * r)));
   }
 }
 
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<LOGM, 
   float2* X = p.X + (int64_t)(item0 + local) * N + (int64_t)rank * M;
   const float sc = p.scale;
   const float sy = p.conj_out ? -sc : sc;
-  auto load = [&](int i) { return src[i]; };
+  auto load = [&](int i) { return __ldcs(src + i); };
   auto emit = [&](int k, float2 v) { X[k] = make_float2(v.x * sc, v.y * sy); };
   __syncthreads();  // tables
   FFT::run(sm, sm_tw, load, emit);
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<LOGM, 
   const float2* C = p.C + (int64_t)(p.sel ? p.sel[c] : c) * N + (int64_t)rank * M;
   float2* out = p.scratch + ((int64_t)local * R + rank) * M;
   auto load = [&](int k) { return cmul(X[k], C[k]); };
-  auto emit = [&](int m, float2 v) { out[m] = cmul(v, twiddle<LOGN, +1>(twN, m * rank)); };
+  auto emit = [&](int m, float2 v) { __stcs(out + m, cmul(v, twiddle<LOGN, +1>(twN, m * rank))); };
   __syncthreads();  // tables
   FFT::run(sm, sm_tw, load, emit);
 }
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(256) k_fsk_corr_b(FskCorrParams p, int item0) 
     const int m = rank * MR + j;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[(int64_t)r * M + m];
+    for (int r = 0; r < R; ++r) v[r] = __ldcs(src + (int64_t)r * M + m);
     dft_reg<R, +1>(v);
 #pragma unroll
     for (int n2 = 0; n2 < R; ++n2) {
