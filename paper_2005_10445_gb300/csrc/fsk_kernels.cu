@@ -27,21 +27,25 @@ namespace atlas {
 constexpr int kFskLogE = 4;  // 16 values per thread in the demodulation transforms
 constexpr int kFskDemodThreads = (1 << kFskLogB) >> kFskLogE;
 
-// padded work buffer, the block's spectrum, |f_1|, twiddle tables
+// padded work buffer, the block's spectrum, twiddle tables (67 KB: three
+// blocks per SM)
 constexpr size_t fsk_demod_smem() {
-  return sizeof(float2) * (BlockFFT<kFskLogB, kFskLogE, -1>::SMEM_ELEMS + (1 << kFskLogB) + TwTables<kFskLogB>::N) +
-         sizeof(float) * (1 << kFskLogB);
+  return sizeof(float2) * (BlockFFT<kFskLogB, kFskLogE, -1>::SMEM_ELEMS + (1 << kFskLogB) + TwTables<kFskLogB>::N);
 }
 
-__global__ void __launch_bounds__(kFskDemodThreads) k_fsk_demod(FskDemodParams p) {
+__global__ void __launch_bounds__(kFskDemodThreads, 3) k_fsk_demod(FskDemodParams p) {
   using FWD = BlockFFT<kFskLogB, kFskLogE, -1>;
   using INV = BlockFFT<kFskLogB, kFskLogE, +1>;
   constexpr int B = 1 << kFskLogB;
+  // The last pass of INV is one radix-E transform per thread: thread t emits
+  // the outputs t + j T, j < E, in increasing j, the same in both inverse
+  // transforms, so |f_1| waits for |f_0| in registers, indexed by j.
+  static_assert(INV::T == kFskDemodThreads && (kFskLogB % kFskLogE) == 0, "one radix-E last pass per thread");
+  constexpr int kLogT = kFskLogB - kFskLogE;
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   float2* Xs = sm + FWD::SMEM_ELEMS;
   float2* sm_tw = Xs + B;
-  float* A1 = reinterpret_cast<float*>(sm_tw + TwTables<kFskLogB>::N);
   load_tables<kFskLogB>(sm_tw, p.tw);
   const int T = p.T;
   const int64_t per = B - (T - 1);
@@ -56,7 +60,7 @@ __global__ void __launch_bounds__(kFskDemodThreads) k_fsk_demod(FskDemodParams p
   const int64_t ring_base = ring ? *p.ring_start : 0;
   const int64_t lo_first = ring ? ring_base : p.lo_first;
   for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
-    __syncthreads();  // tables ready; the previous block is done with Xs and A1
+    __syncthreads();  // tables ready; the previous block is done with Xs
     // transform position n holds input sample i0 + n; outputs n >= T - 1 are
     // the linear convolution at i0 + n (no wrap-around)
     const int64_t i0 = first + blk * per - (T - 1);
@@ -80,9 +84,8 @@ __global__ void __launch_bounds__(kFskDemodThreads) k_fsk_demod(FskDemodParams p
     FWD::run(sm, sm_tw, load, keep);
     __syncthreads();  // the block's spectrum is complete
     auto load1 = [&](int k) { return cmul(Xs[k], p.G1[k]); };
-    // each output index is emitted by the same thread in both inverse
-    // transforms, so A1 needs no barrier between them
-    auto mag1 = [&](int n, float2 v) { A1[n] = sqrtf(fmaf(v.x, v.x, v.y * v.y)); };
+    float a1[1 << kFskLogE];
+    auto mag1 = [&](int n, float2 v) { a1[(n - (int)threadIdx.x) >> kLogT] = sqrtf(fmaf(v.x, v.x, v.y * v.y)); };
     INV::run(sm, sm_tw, load1, mag1);
     auto load0 = [&](int k) { return cmul(Xs[k], p.G0[k]); };
     auto out = [&](int n, float2 v) {
@@ -90,10 +93,10 @@ __global__ void __launch_bounds__(kFskDemodThreads) k_fsk_demod(FskDemodParams p
       if (n < T - 1 || i < p.start || i >= end) return;
       float dd = 0.f, uu = 0.f;
       if (i >= 0 && i < p.S_out) {
-        const float a1 = A1[n];
+        const float m1 = a1[(n - (int)threadIdx.x) >> kLogT];
         const float a0 = sqrtf(fmaf(v.x, v.x, v.y * v.y));
-        const float s = a1 + a0;
-        uu = a1 - a0;
+        const float s = m1 + a0;
+        uu = m1 - a0;
         dd = s > 0.f ? uu / s : 0.f;
       }
       p.d[i - p.start] = dd;
