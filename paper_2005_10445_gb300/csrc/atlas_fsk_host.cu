@@ -77,6 +77,21 @@ struct atlas_fsk_ctx {
   atlas_fsk_detection* d_stage_out = nullptr;
   int stage_cap = 0;
   int* d_stage_count = nullptr;
+  // pinned read-back of the count and the first records (one synchronisation
+  // when they are all)
+  static constexpr int kEager = 64;
+  int* h_eager_count = nullptr;
+  atlas_fsk_detection* h_eager = nullptr;
+  // the input goes to d_stage in kCopyChunks copies on copy_st, so that the
+  // demodulation of the first chunks overlaps the copy of the rest; while
+  // host_chunks is set, run_impl demodulates d_stage chunk by chunk
+  static constexpr int kCopyChunks = 8;
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t ev_main = nullptr;
+  cudaEvent_t ev_copy[kCopyChunks] = {};
+  int64_t copy_end[kCopyChunks] = {};
+  int n_copy = 0;
+  bool host_chunks = false;
   std::string last_error;
   // profiling (atlas_fsk_profile_begin / _end): event pairs per timed launch
   bool profiling = false;
@@ -131,6 +146,12 @@ void free_ctx(atlas_fsk_ctx* ctx) {
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_stage_out);
   cudaFree(ctx->d_stage_count);
+  cudaFreeHost(ctx->h_eager_count);
+  cudaFreeHost(ctx->h_eager);
+  for (auto e : ctx->ev_copy)
+    if (e) cudaEventDestroy(e);
+  if (ctx->ev_main) cudaEventDestroy(ctx->ev_main);
+  if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
   for (auto e : ctx->ev_corr) cudaEventDestroy(e);
   for (auto e : ctx->ev_demod) cudaEventDestroy(e);
   cudaSetDevice(prev);
@@ -415,6 +436,11 @@ struct SampleSource {
   const int16_t* ring = nullptr;
   int64_t ring_cap = 0;
   const int64_t* ring_start = nullptr;
+  // linear input that arrives in chunks: samples [0, chunk_end[k]) are in
+  // place once chunk_ev[k] has completed (chunk_end ascending, the last = S)
+  int n_chunks = 0;
+  const int64_t* chunk_end = nullptr;
+  const cudaEvent_t* chunk_ev = nullptr;
 };
 
 // One launch group of one code-length group: windows [w0, w0 + nw) of a block
@@ -447,7 +473,35 @@ int enqueue_group(atlas_fsk_ctx* ctx, cudaStream_t st, const FskGroup& g, int W,
   dp.u = ctx->d_ubuf;
   const bool td = timed && ctx->profiling && 2 * ctx->demod_used + 1 < (int)ctx->ev_demod.size();
   if (td) CK(cudaEventRecord(ctx->ev_demod[2 * ctx->demod_used], st));
-  CK(atlas::launch_fsk_demod(dp, st));
+  int demod_launches = 1;
+  if (src.n_chunks > 0) {
+    // one launch per input chunk as it arrives.  The demodulation blocks sit
+    // on a grid of multiples of `per` outputs and the chunk ends are on it, so
+    // a launch that ends at a chunk end reads only inputs below it, and every
+    // output is computed by the same block as in one launch.
+    const int64_t per = atlas::fsk_demod_outputs_per_block(ctx->T);
+    const int64_t end = base + len;
+    demod_launches = 0;
+    int k = 0;
+    for (int64_t a = base; a < end;) {
+      while (k < src.n_chunks - 1 && src.chunk_end[k] <= a) ++k;
+      const int64_t e = k < src.n_chunks - 1 ? std::min(end, src.chunk_end[k]) : end;
+      const int64_t need = std::min(S, (std::max<int64_t>(e, 0) + per - 1) / per * per);  // inputs read: [0, need)
+      int kk = 0;
+      while (kk < src.n_chunks - 1 && src.chunk_end[kk] < need) ++kk;
+      CK(cudaStreamWaitEvent(st, src.chunk_ev[kk], 0));
+      atlas::FskDemodParams sub = dp;
+      sub.start = a;
+      sub.count = e - a;
+      sub.d = dp.d + (a - base);
+      sub.u = dp.u + (a - base);
+      CK(atlas::launch_fsk_demod(sub, st));
+      ++demod_launches;
+      a = e;
+    }
+  } else {
+    CK(atlas::launch_fsk_demod(dp, st));
+  }
   if (td) CK(cudaEventRecord(ctx->ev_demod[2 * ctx->demod_used++ + 1], st));
   atlas::FskFwdParams fp;
   fp.d = ctx->d_dbuf;
@@ -496,7 +550,7 @@ int enqueue_group(atlas_fsk_ctx* ctx, cudaStream_t st, const FskGroup& g, int W,
     // transforms: one launch each, or two per pass of the two-pass form
     const int fwd_items = fp.n_items, corr_items = ((nw + 1) / 2) * Cg;
     auto passes = [](int items, int per) { return (items + per - 1) / per; };
-    ctx->prof.launches += 5 + (two_pass ? 2 * passes(fwd_items, fp.chunk_items) : 1) +
+    ctx->prof.launches += 4 + demod_launches + (two_pass ? 2 * passes(fwd_items, fp.chunk_items) : 1) +
                           (two_pass ? 2 * passes(corr_items, cp.chunk_items) : 1);
     ctx->prof.corr_launches += 1;
     ctx->prof.corr_units += (int64_t)nw * Cg;
@@ -574,6 +628,11 @@ int run_impl(atlas_fsk_ctx* ctx, cudaStream_t st, const int16_t* d_iq, int64_t S
   SampleSource src;
   src.iq = d_iq;
   src.first_sample = first_sample;
+  if (ctx->host_chunks && d_iq == ctx->d_stage) {
+    src.n_chunks = ctx->n_copy;
+    src.chunk_end = ctx->copy_end;
+    src.chunk_ev = ctx->ev_copy;
+  }
   for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
     const FskGroup& g = ctx->groups[gi];
     const int W = g.windows(S);
@@ -818,15 +877,55 @@ int atlas_fsk_run_host(atlas_fsk_t ctx, void* stream, const int16_t* h_iq, int64
     if (!ctx->d_stage_count && cudaMalloc((void**)&ctx->d_stage_count, sizeof(int)) != cudaSuccess)
       return ATLAS_ERR_NO_MEMORY;
   }
-  CK(cudaMemcpyAsync(ctx->d_stage, h_iq, sizeof(int16_t) * 2 * (size_t)n_samples, cudaMemcpyHostToDevice, st));
+  if (!ctx->h_eager &&
+      (cudaMallocHost((void**)&ctx->h_eager_count, sizeof(int)) != cudaSuccess ||
+       cudaMallocHost((void**)&ctx->h_eager, sizeof(atlas_fsk_detection) * atlas_fsk_ctx::kEager) != cudaSuccess)) {
+    cudaFreeHost(ctx->h_eager_count);
+    ctx->h_eager_count = nullptr;
+    return ATLAS_ERR_NO_MEMORY;
+  }
+  if (!ctx->copy_st) {
+    CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming));
+    for (auto& e : ctx->ev_copy) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  // chunks end on the demodulation block grid (multiples of `per` samples)
+  const int64_t per = atlas::fsk_demod_outputs_per_block(ctx->T);
+  CK(cudaEventRecord(ctx->ev_main, st));  // earlier work on the stream is done with d_stage
+  CK(cudaStreamWaitEvent(ctx->copy_st, ctx->ev_main, 0));
+  ctx->n_copy = 0;
+  for (int64_t c0 = 0; c0 < n_samples;) {
+    const int k = ctx->n_copy;
+    int64_t c1 = k == atlas_fsk_ctx::kCopyChunks - 1 ? n_samples
+                                                      : ((k + 1) * n_samples / atlas_fsk_ctx::kCopyChunks + per - 1) / per * per;
+    c1 = std::min(std::max(c1, c0 + 1), n_samples);
+    CK(cudaMemcpyAsync(ctx->d_stage + 2 * c0, h_iq + 2 * c0, sizeof(int16_t) * 2 * (size_t)(c1 - c0),
+                       cudaMemcpyHostToDevice, ctx->copy_st));
+    CK(cudaEventRecord(ctx->ev_copy[k], ctx->copy_st));
+    ctx->copy_end[k] = c1;
+    ctx->n_copy = k + 1;
+    c0 = c1;
+  }
+  ctx->host_chunks = true;
   int r = atlas_fsk_run(ctx, stream, ctx->d_stage, n_samples, ctx->d_stage_out, capacity, ctx->d_stage_count);
-  if (r != ATLAS_OK) return r;
-  CK(cudaMemcpyAsync(h_count, ctx->d_stage_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ctx->host_chunks = false;
+  if (r != ATLAS_OK) {
+    cudaStreamSynchronize(ctx->copy_st);  // the copies read the caller's buffer
+    return r;
+  }
+  // the count and up to kEager records in one round trip; the rest after it
+  const int eager = std::min(capacity, atlas_fsk_ctx::kEager);
+  CK(cudaMemcpyAsync(ctx->h_eager_count, ctx->d_stage_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (eager > 0)
+    CK(cudaMemcpyAsync(ctx->h_eager, ctx->d_stage_out, sizeof(atlas_fsk_detection) * (size_t)eager,
+                       cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  *h_count = *ctx->h_eager_count;
   const int n = std::min(*h_count, capacity);
-  if (n > 0) {
-    CK(cudaMemcpyAsync(h_out, ctx->d_stage_out, sizeof(atlas_fsk_detection) * (size_t)n, cudaMemcpyDeviceToHost,
-                       st));
+  if (n > 0) memcpy(h_out, ctx->h_eager, sizeof(atlas_fsk_detection) * (size_t)std::min(n, eager));
+  if (n > eager) {
+    CK(cudaMemcpyAsync(h_out + eager, ctx->d_stage_out + eager, sizeof(atlas_fsk_detection) * (size_t)(n - eager),
+                       cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
   return ATLAS_OK;

@@ -206,6 +206,22 @@ def test_repeat_is_bit_identical_and_host_entry(torch_cuda):
     assert na == nb == nh and a.tobytes() == b.tobytes() == h.tobytes()
 
 
+def test_host_entry_many_records(torch_cuda):
+    """The host-buffer entry with more records than its eager read-back (64):
+    every (window, code) cell reported at threshold 0, equal to the device
+    entry's records; a capacity below the count gives its first records."""
+    torch = torch_cuda
+    w = synth.fsk_realistic(seed=25, seconds=0.05, n_codes=16, n_chips=1024, n_tags=4, snr_range=(-6.0, 0.0))
+    s = make(w, threshold=0.0)
+    iq = torch.from_numpy(np.ascontiguousarray(w.iq16)).cuda()
+    dev, nd = s.run(iq, capacity=8192)
+    host, nh = s.run_host(w.iq16, capacity=8192)
+    Wn = s.windows(0, w.n_samples)[0]
+    assert nd == nh == Wn * 16 > 64 and host.tobytes() == dev.tobytes()
+    part, np_ = s.run_host(w.iq16, capacity=100)
+    assert np_ == nd and part.tobytes() == dev[:100].tobytes()
+
+
 def test_capacity_overflow_reports_required_count(torch_cuda):
     w = synth.fsk_small(seed=11)
     s, full, n = gpu_run(torch_cuda, w)
