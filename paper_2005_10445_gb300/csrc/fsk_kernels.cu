@@ -179,16 +179,24 @@ __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_part(FskStatsPar
   }
 }
 
-// Stage 2: per candidate, the slices summed in order (deterministic), the
-// parabolic arrival time, the record appended to the caller's list.
+// Stage 2: one warp per candidate: lane s takes slice s, the slices are summed
+// by a fixed shuffle tree (deterministic, and log-depth where a sequential
+// FP64 chain was latency-bound), then the parabolic arrival time and the
+// record appended to the caller's list.
+static_assert(kFskStatsSlices == 32, "one slice per lane");
+
 __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_final(FskStatsParams p) {
   const int nc = *p.n_cand;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nc; b += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nc; b += warps) {
+    const double* pv = p.part + ((int64_t)b * kFskStatsSlices + lane) * 5;
+    double v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = warp_sum(pv[k]);
+    if (lane != 0) continue;
     const atlas_detection cd = p.cand[b];
     const int64_t a = (int64_t)cd.window * p.hop + cd.lag;
-    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int sl = 0; sl < kFskStatsSlices; ++sl)
-      for (int k = 0; k < 5; ++k) v[k] += p.part[((int64_t)b * kFskStatsSlices + sl) * 5 + k];
     const double cm = v[0], c0 = v[1], cp = v[2];
     double delta = 0.0;
     if (a - 1 >= 0 && a + 1 <= p.S - p.n_c) {
@@ -345,7 +353,8 @@ cudaError_t launch_fsk_stats(const FskStatsParams& p, int max_cand, cudaStream_t
     k_fsk_stats_part<<<items < resident ? items : resident, kFskStatsThreads, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_fsk_stats_final<<<(max_cand + kFskStatsThreads - 1) / kFskStatsThreads, kFskStatsThreads, 0, s>>>(p);
+    const int warps_per_block = kFskStatsThreads / 32;
+    k_fsk_stats_final<<<(max_cand + warps_per_block - 1) / warps_per_block, kFskStatsThreads, 0, s>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   k_fsk_advance<<<1, 1, 0, s>>>(p.count, p.n_cand);
