@@ -128,7 +128,8 @@ int atlas_acq_windows(atlas_acq_t ctx, int32_t code, int64_t n_samples, int32_t*
  * code) when all codes have the same length -- so repeated runs are
  * bit-identical.  Asynchronous: results are valid after the caller
  * synchronises `stream`.  Allocates nothing.  Returns ATLAS_ERR_INVALID_ARG
- * for bad pointers or sizes, ATLAS_ERR_CUDA if a launch fails.
+ * for bad pointers or sizes or when the current CUDA device is not the one the
+ * context was created on, ATLAS_ERR_CUDA if a launch fails.
  */
 int atlas_acq_run(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t n_samples,
                   atlas_detection* d_out, int32_t capacity, int32_t* d_count);

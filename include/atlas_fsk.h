@@ -107,7 +107,8 @@ int atlas_fsk_windows(atlas_fsk_t ctx, int32_t code, int64_t n_samples, int32_t*
  *   d_count    device, one int32: the number of detections (may exceed capacity;
  *              only the first `capacity` records are written)
  * Detections are ordered by (code length group, window, code).  Asynchronous
- * and stream-ordered; allocates nothing.
+ * and stream-ordered; allocates nothing.  ATLAS_ERR_INVALID_ARG for bad
+ * pointers or sizes or when the current CUDA device is not the context's.
  */
 int atlas_fsk_run(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int64_t n_samples,
                   atlas_fsk_detection* d_out, int32_t capacity, int32_t* d_count);
@@ -131,8 +132,11 @@ int atlas_fsk_run_codes(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int6
                         int32_t capacity, int32_t* d_count);
 
 /* The same with host buffers: copies h_iq in, searches, copies the records and
- * the count out, and synchronises.  Device staging buffers are allocated on
- * first use for a size and kept. */
+ * the count out, and synchronises.  Device staging buffers, a copy stream and
+ * its events are made on first use and kept.  The input goes in eight copies
+ * on the copy stream and the demodulation of each part starts when its copy
+ * is done, so the copy overlaps the computation; the records are those of
+ * atlas_fsk_run on the same samples.  h_iq is read until the call returns. */
 int atlas_fsk_run_host(atlas_fsk_t ctx, void* stream, const int16_t* h_iq, int64_t n_samples,
                        atlas_fsk_detection* h_out, int32_t capacity, int32_t* h_count);
 

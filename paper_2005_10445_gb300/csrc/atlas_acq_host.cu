@@ -470,6 +470,8 @@ int check_run_args(atlas_acq_ctx* ctx, const void* x, int64_t S, const void* out
                    const void* count) {
   if (!ctx || !x || !count || capacity < 0 || (capacity > 0 && !out)) return ATLAS_ERR_INVALID_ARG;
   if (S < ctx->max_L || S > (int64_t)INT32_MAX * 8) return ATLAS_ERR_INVALID_ARG;
+  int dev = 0;  // the workspaces live on the context's device
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device) return ATLAS_ERR_INVALID_ARG;
   return ATLAS_OK;
 }
 

@@ -857,6 +857,8 @@ int atlas_fsk_run_host(atlas_fsk_t ctx, void* stream, const int16_t* h_iq, int64
                        atlas_fsk_detection* h_out, int32_t capacity, int32_t* h_count) {
   if (!ctx || !h_iq || !h_count || capacity < 0 || (capacity > 0 && !h_out)) return ATLAS_ERR_INVALID_ARG;
   if (n_samples < ctx->max_nc || n_samples > ((int64_t)1 << 40)) return ATLAS_ERR_INVALID_ARG;
+  int dev = 0;  // the staging buffers and the copy stream live on the context's device
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device) return ATLAS_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   if (ctx->stage_samples < n_samples) {
     cudaFree(ctx->d_stage);
