@@ -896,16 +896,17 @@ int atlas_fsk_run_host(atlas_fsk_t ctx, void* stream, const int16_t* h_iq, int64
   CK(cudaEventRecord(ctx->ev_main, st));  // earlier work on the stream is done with d_stage
   CK(cudaStreamWaitEvent(ctx->copy_st, ctx->ev_main, 0));
   ctx->n_copy = 0;
-  for (int64_t c0 = 0; c0 < n_samples;) {
-    const int k = ctx->n_copy;
-    int64_t c1 = k == atlas_fsk_ctx::kCopyChunks - 1 ? n_samples
-                                                      : ((k + 1) * n_samples / atlas_fsk_ctx::kCopyChunks + per - 1) / per * per;
-    c1 = std::min(std::max(c1, c0 + 1), n_samples);
+  int64_t c0 = 0;
+  for (int k = 0; k < atlas_fsk_ctx::kCopyChunks; ++k) {
+    const int64_t c1 = k == atlas_fsk_ctx::kCopyChunks - 1
+                           ? n_samples
+                           : std::min(n_samples, ((k + 1) * n_samples / atlas_fsk_ctx::kCopyChunks + per - 1) / per * per);
+    if (c1 <= c0) continue;  // short streams: fewer, whole-block chunks
+    const int j = ctx->n_copy++;
     CK(cudaMemcpyAsync(ctx->d_stage + 2 * c0, h_iq + 2 * c0, sizeof(int16_t) * 2 * (size_t)(c1 - c0),
                        cudaMemcpyHostToDevice, ctx->copy_st));
-    CK(cudaEventRecord(ctx->ev_copy[k], ctx->copy_st));
-    ctx->copy_end[k] = c1;
-    ctx->n_copy = k + 1;
+    CK(cudaEventRecord(ctx->ev_copy[j], ctx->copy_st));
+    ctx->copy_end[j] = c1;
     c0 = c1;
   }
   ctx->host_chunks = true;
