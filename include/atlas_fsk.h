@@ -133,7 +133,7 @@ int atlas_fsk_run_codes(atlas_fsk_t ctx, void* stream, const int16_t* d_iq, int6
 
 /* The same with host buffers: copies h_iq in, searches, copies the records and
  * the count out, and synchronises.  Device staging buffers, a copy stream and
- * its events are made on first use and kept.  The input goes in eight copies
+ * its events are made on first use and kept.  The input goes in four copies
  * on the copy stream and the demodulation of each part starts when its copy
  * is done, so the copy overlaps the computation; the records are those of
  * atlas_fsk_run on the same samples.  h_iq is read until the call returns. */

@@ -85,7 +85,7 @@ struct atlas_fsk_ctx {
   // the input goes to d_stage in kCopyChunks copies on copy_st, so that the
   // demodulation of the first chunks overlaps the copy of the rest; while
   // host_chunks is set, run_impl demodulates d_stage chunk by chunk
-  static constexpr int kCopyChunks = 8;
+  static constexpr int kCopyChunks = 4;
   cudaStream_t copy_st = nullptr;
   cudaEvent_t ev_main = nullptr;
   cudaEvent_t ev_copy[kCopyChunks] = {};

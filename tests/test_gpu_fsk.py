@@ -222,6 +222,23 @@ def test_host_entry_many_records(torch_cuda):
     assert np_ == nd and part.tobytes() == dev[:100].tobytes()
 
 
+@pytest.mark.parametrize("extra", [0, 1000, 11000, 37400])
+def test_host_entry_equals_device_entry(torch_cuda, extra):
+    """Streams from one support long (one copy chunk) to many demodulation
+    blocks (eight chunks): the host entry's chunked copy and demodulation give
+    the device entry's records bit for bit (threshold 0: every cell)."""
+    torch = torch_cuda
+    w0 = synth.fsk_small(seed=16, n_tags=0)
+    n_c = make(w0).windows(0, w0.n_samples)[3]
+    w = synth.fsk_stream(16, n_c + extra, w0.chips, w0.sps, w0.fs_hz, w0.f1_hz, w0.f0_hz, w0.f_lo_hz, 2,
+                         (-3.0, 0.0))
+    s = make(w, threshold=0.0)
+    iq = torch.from_numpy(np.ascontiguousarray(w.iq16)).cuda()
+    dev, nd = s.run(iq, capacity=4096)
+    host, nh = s.run_host(w.iq16, capacity=4096)
+    assert nd == nh >= 1 and host.tobytes() == dev.tobytes()
+
+
 def test_capacity_overflow_reports_required_count(torch_cuda):
     w = synth.fsk_small(seed=11)
     s, full, n = gpu_run(torch_cuda, w)
