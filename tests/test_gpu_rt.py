@@ -21,9 +21,9 @@ def torch_cuda(built_lib):
     return torch
 
 
-def make_rt(w, periods, **opt):
+def make_rt(w, periods, fft_len=0, **opt):
     from paper_2005_10445_gb300.binding import FskSearch, Runtime, rt_default_opts
-    s = FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp)
+    s = FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp, fft_len=fft_len)
     o = rt_default_opts(w.fs_hz)
     for k, v in opt.items():
         setattr(o, k, v)
@@ -201,3 +201,23 @@ def test_runtime_codes_of_two_lengths(torch_cuda):
         mine = ev[ev["code"] == c]
         assert np.sum(mine["kind"] == b.RT_SEARCH_DETECTION) >= 1
         assert np.sum(mine["kind"] == b.RT_TRACK_DETECTION) >= 2, c
+
+
+def test_runtime_over_a_two_pass_plan(torch_cuda):
+    """An FSK context with N = 2^18 (sixteen blocks of 2^14 points, two passes,
+    forward and inverse): searching blocks of two windows, tracking blocks of
+    one zero-padded window run as captured graphs.  Every tag is found and
+    then tracked at each transmission, within two samples of its delay."""
+    from paper_2005_10445_gb300 import binding as b
+    # periods above N / fs, so a window holds at most one transmission of a code
+    w, periods = synth.fsk_periodic(seed=14, seconds=1.2, n_codes=3, period_s=(0.07, 0.09))
+    rt, o = make_rt(w, periods, fft_len=1 << 18)
+    ev = feed(rt, w, 160000)
+    assert not np.any(np.isin(ev["kind"], [b.RT_TRACK_MISS, b.RT_TRACK_LOST, b.RT_SEARCH_SKIPPED]))
+    for c in range(3):
+        mine = ev[ev["code"] == c]
+        assert np.sum(mine["kind"] == b.RT_SEARCH_DETECTION) >= 1
+        assert np.sum(mine["kind"] == b.RT_TRACK_DETECTION) >= 5, c
+        truth = np.array([t.delay for t in w.tags if t.code == c])
+        for e in mine:
+            assert np.min(np.abs(truth - e["toa"])) <= 2.0
