@@ -92,9 +92,14 @@ __device__ __forceinline__ void bfly(float2& a, float2& b) {
     const float py = fmaf(b.x, wi, fmaf(b.y, wr, a.y));
     b = make_float2(fmaf(2.f, a.x, -px), fmaf(2.f, a.y, -py));
     a = make_float2(px, py);
+  } else if constexpr (K == 0) {
+    // w = 1: two packed FP32x2 operations; a - b = fma(b, -1, a) exactly
+    const float2 s = __fadd2_rn(a, b);
+    b = __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+    a = s;
   } else {
-    // w = 1, or w = -/+ i (a swap of the parts)
-    const float2 t = (K == 0) ? b : ((DIR < 0) ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x));
+    // w = -/+ i (a swap of the parts)
+    const float2 t = (DIR < 0) ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);
     b = make_float2(a.x - t.x, a.y - t.y);
     a = make_float2(a.x + t.x, a.y + t.y);
   }
