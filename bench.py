@@ -89,9 +89,10 @@ def fsk_ncu_traffic_per_cell():
         return None
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the correlation kernel from the committed ncu
-    summary, if it was taken on the current kernel source and launch size."""
+def ncu_traffic(units_per_launch: float):
+    """DRAM bytes of the correlation kernel from the committed ncu summary,
+    scaled from the captured full launch to a launch of `units_per_launch`
+    cells, if the summary was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "k_corr_realistic_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -103,8 +104,8 @@ def ncu_traffic():
     if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_full_launch"])
-    except (KeyError, ValueError):
+        return float(vals["dram_bytes_per_full_launch"]) * units_per_launch / float(vals["cells_per_full_launch"])
+    except (KeyError, ValueError, ZeroDivisionError):
         return None
 
 
@@ -848,7 +849,7 @@ def main() -> None:
     units_per_launch = prof["corr_units"] / max(prof["corr_launches"], 1)
     corr_avg_ms = prof["corr_ms"] / max(prof["timed_launches"], 1)
     achieved = units_per_launch * flops_per_cell(N) / (corr_avg_ms / 1e3) / 1e12
-    traffic = ncu_traffic()
+    traffic = ncu_traffic(units_per_launch)
     hbm_bytes_step = S * 8 * (N / (N - len(wl.chips[0]) * wl.sps)) + len(wl.chips) * N * 8
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
