@@ -163,6 +163,16 @@ def test_two_pass_only_plans(torch_cuda, fft_len, block_log2, seconds):
     compare(dets, ora)
 
 
+def test_launch_groups_at_2_18_do_not_change_results(torch_cuda):
+    """N = 2^18 in launch groups of 2 windows (several passes of the two-pass
+    forms, each with its own scratch fill) against one group: bit-identical."""
+    w = synth.fsk_realistic(seed=26, seconds=0.2, n_codes=3, n_tags=4, snr_range=(-12.0, -3.0),
+                            fft_len=1 << 18)
+    _, ref, n_ref = gpu_run(torch_cuda, w, threshold=0.0)
+    _, got, n = gpu_run(torch_cuda, w, threshold=0.0, windows_per_launch=2)
+    assert n == n_ref >= 3 * 7 and got.tobytes() == ref.tobytes()
+
+
 def test_block_sizes_agree_at_2_17(torch_cuda):
     """N = 2^17 as sixteen blocks of 2^13 points or eight of 2^14: different
     factorisations of the same transform, the same detections with scores and
