@@ -303,18 +303,52 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams p) {
     const uint64_t inc = p.inc[det.freq_bin];
     // y[m] = x[m] exp(-2 pi i f m / fs) for m in [a-1, a+L]: the phase is the exact
     // 64-bit fixed-point product m * inc, the rotation FP32; the three direct
-    // correlations sum_n y[a+d+n] r[n] (d = -1, 0, +1) accumulate in FP64.
+    // correlations sum_n y[a+d+n] r[n] (d = -1, 0, +1).
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t m = a - 1 + threadIdx.x; m <= a + L; m += kRefineThreads) {
-      if (m < 0 || m >= p.S) continue;
-      const float2 y = cmul(p.x[m], expi_neg(inc * (uint64_t)m));
+    if (sps >= 2) {
+      // r is constant over a chip, so a thread takes runs of sps samples
+      // m = a - 1 + k sps + s: for lag d = j - 1 (j <= 2 <= sps) the samples
+      // s < j belong to chip k - 1 and the others to chip k.  Each chip's
+      // samples are summed in FP32 (at most sps terms), the run's two chip
+      // sums combined with their signs in FP32, and the runs accumulate in
+      // FP64: one FP64 addition per run and component, not one per sample.
+      const int n_chips = L / sps;
+      for (int64_t k = threadIdx.x; k <= n_chips; k += kRefineThreads) {
+        const int64_t m0 = a - 1 + k * sps;
+        float2 lo[3] = {}, hi[3] = {};
+        for (int s = 0; s < sps; ++s) {
+          const int64_t m = m0 + s;
+          if (m > a + L) break;
+          if (m < 0 || m >= p.S) continue;
+          const float2 y = cmul(p.x[m], expi_neg(inc * (uint64_t)m));
 #pragma unroll
-      for (int d = -1; d <= 1; ++d) {
-        const int64_t nn = m - a - d;
-        if (nn >= 0 && nn < L) {
-          const bool neg = ch[nn / sps] < 0;
-          acc[2 * (d + 1)] += neg ? -(double)y.x : (double)y.x;
-          acc[2 * (d + 1) + 1] += neg ? -(double)y.y : (double)y.y;
+          for (int j = 0; j < 3; ++j) {
+            float2& t = s < j ? lo[j] : hi[j];
+            t.x += y.x;
+            t.y += y.y;
+          }
+        }
+        const float sk = k < n_chips ? (ch[k] < 0 ? -1.f : 1.f) : 0.f;   // chip k
+        const float sk1 = k >= 1 ? (ch[k - 1] < 0 ? -1.f : 1.f) : 0.f;   // chip k - 1
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          acc[2 * j] += (double)fmaf(sk, hi[j].x, sk1 * lo[j].x);
+          acc[2 * j + 1] += (double)fmaf(sk, hi[j].y, sk1 * lo[j].y);
+        }
+      }
+    } else {
+      // one sample per chip: every term accumulates in FP64
+      for (int64_t m = a - 1 + threadIdx.x; m <= a + L; m += kRefineThreads) {
+        if (m < 0 || m >= p.S) continue;
+        const float2 y = cmul(p.x[m], expi_neg(inc * (uint64_t)m));
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+          const int64_t nn = m - a - d;
+          if (nn >= 0 && nn < L) {
+            const bool neg = ch[nn] < 0;
+            acc[2 * (d + 1)] += neg ? -(double)y.x : (double)y.x;
+            acc[2 * (d + 1) + 1] += neg ? -(double)y.y : (double)y.y;
+          }
         }
       }
     }
