@@ -51,8 +51,8 @@ typedef struct {
   int32_t lag;     /* window-relative lag j; absolute lag a = window * hop_c + lag */
   float   score;   /* corr[j]^2 / floor (FP32 transform path) */
   double  toa;     /* a + delta, samples from the stream start */
-  double  w_c;     /* sum_n d_c[n] d[a+n]  (direct sums of the FP32 d, u, d_c: FP32 over at most 9
-                      terms per thread, FP64 beyond) */
+  double  w_c;     /* sum_n d_c[n] d[a+n]  (direct sums of the FP32 d, u, d_c: FP32 within a warp,
+                      at most 32 x 9 terms, FP64 beyond) */
   double  q;       /* sum_n d[a+n]^2 */
   double  p_c;     /* sum_n d_c[n] u[a+n] */
 } atlas_fsk_detection;

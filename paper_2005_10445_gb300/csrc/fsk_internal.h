@@ -112,7 +112,7 @@ struct FskCorrParams {
 };
 
 // Per candidate of a launch group: the direct sums at the peak (FP32 within a
-// thread's few terms, FP64 beyond) and the
+// warp's few terms per thread and its shuffle tree, FP64 beyond) and the
 // parabolic arrival time (step 8); appends to the caller's list.
 struct FskStatsParams {
   const atlas_detection* cand;  // group's candidates (k_select output)

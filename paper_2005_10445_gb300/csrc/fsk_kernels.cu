@@ -10,8 +10,9 @@
 //   k_fsk_stats_part / _final
 //                  step 8 per candidate: w_c, q, p_c and the three
 //                  correlation values around the peak as direct sums over the
-//                  support (32 slices; FP32 within a thread's few terms, FP64
-//                  across threads and slices, in a fixed order), the parabolic
+//                  support (32 slices; FP32 within a warp's few terms per
+//                  thread and its shuffle tree, FP64 across warps and slices,
+//                  in a fixed order), the parabolic
 //                  arrival time, the record appended to the caller's list
 //   k_fsk_select   per (window, code): combines the cluster's partial results,
 //                  score, threshold, ordered compaction by a block prefix sum
@@ -118,6 +119,12 @@ __global__ void k_fsk_replica(FskReplicaParams p, int L) {
   }
 }
 
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_part(FskStatsPar
       return (k >= 0 && k < p.len) ? p.d[k] : 0.f;
     };
     // each thread sums its few terms (a slice of chunk <= 2100 over 256 threads)
-    // in FP32; the partial sums are combined in FP64
+    // in FP32
     float fm = 0.f, f0 = 0.f, fp = 0.f, fq = 0.f, fu = 0.f;
     const int n1 = min(p.n_c, (sl + 1) * chunk);
     for (int n = sl * chunk + threadIdx.x; n < n1; n += blockDim.x) {
@@ -157,11 +164,13 @@ __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_part(FskStatsPar
       fq = fmaf(d0, d0, fq);
       fu = fmaf(g, u0, fu);
     }
-    double cm = warp_sum((double)fm);
-    double c0 = warp_sum((double)f0);
-    double cp = warp_sum((double)fp);
-    double q = warp_sum((double)fq);
-    double pc = warp_sum((double)fu);
+    // a warp's partial sums (at most 32 x 9 terms) by an FP32 shuffle tree;
+    // FP64 across the warps and slices
+    const double cm = warp_sumf(fm);
+    const double c0 = warp_sumf(f0);
+    const double cp = warp_sumf(fp);
+    const double q = warp_sumf(fq);
+    const double pc = warp_sumf(fu);
     __syncthreads();  // the previous item's reduction has been read
     if (lane == 0) {
       red[0][warp] = cm;
