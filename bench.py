@@ -654,7 +654,8 @@ def run_stream(args, rank: int, world: int, dev, torch, dist) -> None:
                                     period_s=(0.4, 0.6), snr_range=(-15.0, 0.0), f_lo_hz=1e6, offset_hz=5e3)
     S = w.n_samples
     chunk = int(0.01 * fs)
-    fsk_s = binding.FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp)
+    fsk_s = binding.FskSearch(w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp,
+                              exchange=args.fsk_exchange)
     opts = binding.rt_default_opts(fs)
     iq = np.ascontiguousarray(w.iq16)
     st = torch.cuda.current_stream(dev).cuda_stream
@@ -743,6 +744,8 @@ def main() -> None:
     ap.add_argument("--fsk-fft-len", type=int, default=1 << 18,
                     help="FSK workload: N (0 = the library default, 2 nextpow2(L) = 2^17 here)")
     ap.add_argument("--fsk-block-log2", type=int, default=0, help="FSK workload: log2 points per block (0 = default)")
+    ap.add_argument("--fsk-exchange", type=int, default=0,
+                    help="stream workload: exchange form of the FSK transforms (0 = default, 1 = cluster, 2 = two passes)")
     ap.add_argument("--workload", default="realistic", choices=["realistic", "batching", "learned", "precision", "fsk", "stream"])
     ap.add_argument("--train-windows", type=int, default=20000)
     ap.add_argument("--test-windows", type=int, default=2000)

@@ -661,12 +661,22 @@ struct atlas_fsk_tracker {
     int32_t local;    // the code's index within its group
     int32_t global;   // the code
   };
-  Desc* h_desc = nullptr;  // pinned: copied in by the graph's first node
-  Desc* d_desc = nullptr;
-  atlas_fsk_detection* d_out = nullptr;
+  // One block of device memory, mirrored by one pinned host block:
+  //   [0, 16)   Desc
+  //   [16, 32)  the record count (int32, then padding)
+  //   [32, ..)  W records
+  // The graph's first node copies [0, 32) in (the descriptor and a zero
+  // count) and its last node copies [16, ..) out (the count and the records).
+  static constexpr size_t kCount = 16, kRecords = 32;
+  char* d_blk = nullptr;
+  char* h_blk = nullptr;
+  Desc* d_desc = nullptr;                // views into d_blk / h_blk
+  Desc* h_desc = nullptr;
   int* d_count = nullptr;
-  atlas_fsk_detection* h_out = nullptr;  // pinned: copied out by the graph's last nodes
   int* h_count = nullptr;
+  atlas_fsk_detection* d_out = nullptr;
+  atlas_fsk_detection* h_out = nullptr;
+  size_t blk_bytes() const { return kRecords + sizeof(atlas_fsk_detection) * (size_t)W; }
   cudaStream_t cs = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -679,12 +689,8 @@ void free_tracker(atlas_fsk_tracker* t) {
   if (t->exec) cudaGraphExecDestroy(t->exec);
   if (t->graph) cudaGraphDestroy(t->graph);
   if (t->cs) cudaStreamDestroy(t->cs);
-  cudaFreeHost(t->h_desc);
-  cudaFreeHost(t->h_out);
-  cudaFreeHost(t->h_count);
-  cudaFree(t->d_desc);
-  cudaFree(t->d_out);
-  cudaFree(t->d_count);
+  cudaFreeHost(t->h_blk);
+  cudaFree(t->d_blk);
   delete t;
 }
 
@@ -698,15 +704,14 @@ int capture_tracker(atlas_fsk_tracker* t, const int16_t* d_ring, int64_t ring_sa
   src.ring_cap = ring_samples;
   src.ring_start = &t->d_desc->start;
   int r = ATLAS_OK;
-  cudaError_t e = cudaMemcpyAsync(t->d_desc, t->h_desc, sizeof(atlas_fsk_tracker::Desc), cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaMemsetAsync(t->d_count, 0, sizeof(int), cs);
+  // the descriptor and a zero count in one copy
+  cudaError_t e = cudaMemcpyAsync(t->d_blk, t->h_blk, atlas_fsk_tracker::kRecords, cudaMemcpyHostToDevice, cs);
   for (int w0 = 0; e == cudaSuccess && r == ATLAS_OK && w0 < t->W; w0 += ctx->wc)
     r = enqueue_group(ctx, cs, g, t->W, w0, std::min(ctx->wc, t->W - w0), t->len, src, 1, &t->d_desc->local,
                       &t->d_desc->global, t->d_out, t->W, t->d_count, false);
-  if (e == cudaSuccess && r == ATLAS_OK)
-    e = cudaMemcpyAsync(t->h_count, t->d_count, sizeof(int), cudaMemcpyDeviceToHost, cs);
-  if (e == cudaSuccess && r == ATLAS_OK)
-    e = cudaMemcpyAsync(t->h_out, t->d_out, sizeof(atlas_fsk_detection) * (size_t)t->W, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && r == ATLAS_OK)  // the count and the records in one copy
+    e = cudaMemcpyAsync(t->h_blk + atlas_fsk_tracker::kCount, t->d_blk + atlas_fsk_tracker::kCount,
+                        t->blk_bytes() - atlas_fsk_tracker::kCount, cudaMemcpyDeviceToHost, cs);
   const cudaError_t e_end = cudaStreamEndCapture(cs, &t->graph);  // always leaves capture mode
   if (r != ATLAS_OK) return r;
   if (e != cudaSuccess) return fail_cuda(ctx, e);
@@ -733,15 +738,19 @@ int atlas_fsk_tracker_create(atlas_fsk_tracker_t* out, atlas_fsk_t ctx, int32_t 
   t->gi = gi;
   t->len = n_samples;
   t->W = g.windows(n_samples);
-  if (cudaMallocHost((void**)&t->h_desc, sizeof(atlas_fsk_tracker::Desc)) != cudaSuccess ||
-      cudaMallocHost((void**)&t->h_out, sizeof(atlas_fsk_detection) * (size_t)t->W) != cudaSuccess ||
-      cudaMallocHost((void**)&t->h_count, sizeof(int)) != cudaSuccess ||
-      cudaMalloc((void**)&t->d_desc, sizeof(atlas_fsk_tracker::Desc)) != cudaSuccess ||
-      cudaMalloc((void**)&t->d_out, sizeof(atlas_fsk_detection) * (size_t)t->W) != cudaSuccess ||
-      cudaMalloc((void**)&t->d_count, sizeof(int)) != cudaSuccess) {
+  static_assert(sizeof(atlas_fsk_tracker::Desc) <= atlas_fsk_tracker::kCount, "descriptor fits its slot");
+  if (cudaMallocHost((void**)&t->h_blk, t->blk_bytes()) != cudaSuccess ||
+      cudaMalloc((void**)&t->d_blk, t->blk_bytes()) != cudaSuccess) {
     free_tracker(t);
     return ATLAS_ERR_NO_MEMORY;
   }
+  memset(t->h_blk, 0, t->blk_bytes());
+  t->d_desc = reinterpret_cast<atlas_fsk_tracker::Desc*>(t->d_blk);
+  t->h_desc = reinterpret_cast<atlas_fsk_tracker::Desc*>(t->h_blk);
+  t->d_count = reinterpret_cast<int*>(t->d_blk + atlas_fsk_tracker::kCount);
+  t->h_count = reinterpret_cast<int*>(t->h_blk + atlas_fsk_tracker::kCount);
+  t->d_out = reinterpret_cast<atlas_fsk_detection*>(t->d_blk + atlas_fsk_tracker::kRecords);
+  t->h_out = reinterpret_cast<atlas_fsk_detection*>(t->h_blk + atlas_fsk_tracker::kRecords);
   memset(t->h_desc, 0, sizeof(atlas_fsk_tracker::Desc));
   int r = ATLAS_OK;
   if (cudaStreamCreateWithFlags(&t->cs, cudaStreamNonBlocking) != cudaSuccess) r = ATLAS_ERR_CUDA;
@@ -765,6 +774,7 @@ int atlas_fsk_tracker_run(atlas_fsk_tracker_t t, void* stream, int32_t code, int
   t->h_desc->start = block_start;
   t->h_desc->local = local;
   t->h_desc->global = code;
+  *t->h_count = 0;  // copied in with the descriptor
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaGraphLaunch(t->exec, st));
   CK(cudaStreamSynchronize(st));  // the descriptor has been read, the results are in
