@@ -725,8 +725,8 @@ def run_stream(args, rank: int, world: int, dev, torch, dist) -> None:
                      "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, max clock)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": S * 4,
                 "d2h_bytes_per_step": "per task: the count and its records"},
-        # searching tasks' kernels (counted by the library) plus the 7 kernels of each tracking graph launch
-        "gpu_launches": prof["launches"] // max(args.steps, 1) + 7 * stats["track_tasks"],
+        # searching tasks' kernels (counted by the library) plus the kernel nodes of the tracking graph launches
+        "gpu_launches": prof["launches"] // max(args.steps, 1) + stats["track_kernels"],
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -170,6 +170,9 @@ int atlas_fsk_tracker_create(atlas_fsk_tracker_t* out, atlas_fsk_t ctx, int32_t 
                              const int16_t* d_ring, int64_t ring_samples);
 int atlas_fsk_tracker_run(atlas_fsk_tracker_t t, void* stream, int32_t code, int64_t block_start,
                           atlas_fsk_detection* h_out, int32_t capacity, int32_t* h_count);
+/* Kernel launches one atlas_fsk_tracker_run makes (the kernel nodes of its
+ * graph); -1 for a null tracker. */
+int32_t atlas_fsk_tracker_kernels(atlas_fsk_tracker_t t);
 void atlas_fsk_tracker_destroy(atlas_fsk_tracker_t t);
 
 /* Device-time profile of the runs between begin and end: CUDA events on the

@@ -78,6 +78,7 @@ typedef struct {
   int64_t searched_samples;  /* samples covered by searching blocks (overlaps counted twice) */
   int64_t search_units, track_units;  /* work units (samples x codes) of each kind */
   int64_t events;
+  int64_t track_kernels;   /* kernel launches of the tracking tasks (their graphs' kernel nodes) */
   double  search_ms, track_ms;  /* host wall-clock time of the tasks of each kind, from launch to results */
   int32_t searching, tracking;  /* codes in each queue now */
   int32_t reserved;

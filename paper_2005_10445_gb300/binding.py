@@ -49,7 +49,7 @@ EXPORTED_FSK = [
     "atlas_fsk_default_opts", "atlas_fsk_create", "atlas_fsk_windows", "atlas_fsk_run", "atlas_fsk_run_codes",
     "atlas_fsk_run_host",
     "atlas_fsk_demod", "atlas_fsk_code_demod", "atlas_fsk_profile_begin", "atlas_fsk_profile_end",
-    "atlas_fsk_tracker_create", "atlas_fsk_tracker_run", "atlas_fsk_tracker_destroy",
+    "atlas_fsk_tracker_create", "atlas_fsk_tracker_run", "atlas_fsk_tracker_kernels", "atlas_fsk_tracker_destroy",
     "atlas_fsk_last_error", "atlas_fsk_destroy",
 ]
 
@@ -103,7 +103,8 @@ class RtOpts(ctypes.Structure):
 class RtStats(ctypes.Structure):
     _fields_ = [("pushed", ctypes.c_int64), ("search_tasks", ctypes.c_int64), ("track_tasks", ctypes.c_int64),
                 ("searched_samples", ctypes.c_int64), ("search_units", ctypes.c_int64),
-                ("track_units", ctypes.c_int64), ("events", ctypes.c_int64), ("search_ms", ctypes.c_double),
+                ("track_units", ctypes.c_int64), ("events", ctypes.c_int64), ("track_kernels", ctypes.c_int64),
+                ("search_ms", ctypes.c_double),
                 ("track_ms", ctypes.c_double), ("searching", ctypes.c_int32), ("tracking", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
@@ -232,6 +233,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_fsk_tracker_create.restype = ctypes.c_int
     lib.atlas_fsk_tracker_run.argtypes = [vp, vp, i32, i64, vp, i32, ctypes.POINTER(i32)]
     lib.atlas_fsk_tracker_run.restype = ctypes.c_int
+    lib.atlas_fsk_tracker_kernels.argtypes = [vp]
+    lib.atlas_fsk_tracker_kernels.restype = i32
     lib.atlas_fsk_tracker_destroy.argtypes = [vp]
     lib.atlas_fsk_tracker_destroy.restype = None
     lib.atlas_fsk_last_error.argtypes = [vp]
@@ -783,6 +786,10 @@ class FskTracker:
         _check_fsk(self._lib.atlas_fsk_tracker_run(self.t, stream, code, block_start, out.ctypes.data, capacity,
                                                    ctypes.byref(n)), self.fsk.ctx)
         return out[: min(n.value, capacity)].copy(), n.value
+
+    def kernels(self) -> int:
+        """Kernel launches one run makes (the kernel nodes of the graph)."""
+        return int(self._lib.atlas_fsk_tracker_kernels(self.t))
 
     def close(self) -> None:
         if self.t:

@@ -550,15 +550,17 @@ int enqueue_group(atlas_fsk_ctx* ctx, cudaStream_t st, const FskGroup& g, int W,
     // transforms: one launch each, or two per pass of the two-pass form
     const int fwd_items = fp.n_items, corr_items = ((nw + 1) / 2) * Cg;
     auto passes = [](int items, int per) { return (items + per - 1) / per; };
-    ctx->prof.launches += 4 + demod_launches + (two_pass ? 2 * passes(fwd_items, fp.chunk_items) : 1) +
+    // select and the two peak-sum stages, and the count's advance unless the
+    // final stage does it (small groups)
+    ctx->prof.launches += 3 + (nw * Cg > atlas::kFskStatsFinalOneBlock ? 1 : 0) + demod_launches +
+                          (two_pass ? 2 * passes(fwd_items, fp.chunk_items) : 1) +
                           (two_pass ? 2 * passes(corr_items, cp.chunk_items) : 1);
     ctx->prof.corr_launches += 1;
     ctx->prof.corr_units += (int64_t)nw * Cg;
     ctx->prof.demod_launches += 1;
     ctx->prof.demod_samples += len;
   }
-  CK(cudaMemsetAsync(ctx->d_ncand, 0, sizeof(int), st));
-  atlas::SelectParams sp;
+  atlas::SelectParams sp;  // writes the group's candidate count (the list starts empty)
   sp.part = ctx->d_part;
   sp.codes = d_sel_global;
   sp.Cg = Cg;
@@ -680,6 +682,7 @@ struct atlas_fsk_tracker {
   cudaStream_t cs = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int kernels = 0;  // kernel nodes of the graph
 };
 
 namespace {
@@ -717,6 +720,16 @@ int capture_tracker(atlas_fsk_tracker* t, const int16_t* d_ring, int64_t ring_sa
   if (e != cudaSuccess) return fail_cuda(ctx, e);
   if (e_end != cudaSuccess) return fail_cuda(ctx, e_end);
   CK(cudaGraphInstantiate(&t->exec, t->graph, 0));
+  size_t n_nodes = 0;
+  CK(cudaGraphGetNodes(t->graph, nullptr, &n_nodes));
+  std::vector<cudaGraphNode_t> nodes(n_nodes);
+  if (n_nodes) CK(cudaGraphGetNodes(t->graph, nodes.data(), &n_nodes));
+  t->kernels = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    CK(cudaGraphNodeGetType(nd, &ty));
+    t->kernels += ty == cudaGraphNodeTypeKernel;
+  }
   return ATLAS_OK;
 }
 
@@ -783,6 +796,8 @@ int atlas_fsk_tracker_run(atlas_fsk_tracker_t t, void* stream, int32_t code, int
   *h_count = *t->h_count;
   return ATLAS_OK;
 }
+
+int32_t atlas_fsk_tracker_kernels(atlas_fsk_tracker_t t) { return t ? t->kernels : -1; }
 
 void atlas_fsk_tracker_destroy(atlas_fsk_tracker_t t) { free_tracker(t); }
 

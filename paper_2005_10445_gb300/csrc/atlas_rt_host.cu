@@ -292,6 +292,7 @@ int atlas_rt_pump(atlas_rt_t rt, void* stream, int32_t max_tasks, atlas_rt_event
       if (r != ATLAS_OK) return r;
       rt->st.track_ms += elapsed_ms();
       rt->st.track_tasks += 1;
+      rt->st.track_kernels += atlas_fsk_tracker_kernels(rt->trackers[rt->n_c[tc]]);
       rt->st.track_units += TB;
       if (n > 0) {
         const atlas_fsk_detection& d = rt->h_out[0];

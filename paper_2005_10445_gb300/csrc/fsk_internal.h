@@ -137,8 +137,13 @@ cudaError_t launch_fsk_replica(const FskReplicaParams& p, int n_codes, int L, cu
 // N = 2^logN points as 2^(logN - logM) blocks of 2^logM (fsk_plan_supported)
 cudaError_t launch_fsk_fwd(int logN, int logM, const FskFwdParams& p, cudaStream_t s);
 cudaError_t launch_fsk_corr(int logN, int logM, const FskCorrParams& p, cudaStream_t s);
-// selection of a launch group (SelectParams with K = 1, sps = R partials per cell)
+// selection of a launch group (SelectParams with K = 1, sps = R partials per
+// cell); *p.count receives the group's candidate count (not accumulated)
 cudaError_t launch_fsk_select(const SelectParams& p, cudaStream_t s);
+// the peak sums of up to max_cand candidates, then *p.count += *p.n_cand: in
+// the final stage's single block when max_cand <= kFskStatsFinalOneBlock,
+// else by a separate one-thread launch
+constexpr int kFskStatsFinalOneBlock = 32;
 cudaError_t launch_fsk_stats(const FskStatsParams& p, int max_cand, cudaStream_t s);
 
 }  // namespace atlas

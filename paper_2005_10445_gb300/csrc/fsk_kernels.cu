@@ -194,6 +194,9 @@ __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_part(FskStatsPar
 // record appended to the caller's list.
 static_assert(kFskStatsSlices == 32, "one slice per lane");
 
+// ADVANCE (a one-block launch): the block also advances the caller's running
+// count once every record is written, in place of k_fsk_advance.
+template <bool ADVANCE>
 __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_final(FskStatsParams p) {
   const int nc = *p.n_cand;
   const int lane = threadIdx.x & 31;
@@ -230,6 +233,10 @@ __global__ void __launch_bounds__(kFskStatsThreads) k_fsk_stats_final(FskStatsPa
       p.out[idx] = o;
     }
   }
+  if constexpr (ADVANCE) {
+    __syncthreads();  // every record has read the old count
+    if (threadIdx.x == 0) *p.count += nc;
+  }
 }
 
 __global__ void k_fsk_advance(int* count, const int* n) { *count += *n; }
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(kFskSelectThreads) k_fsk_select(SelectParams p
   __shared__ int warp_tot[kFskSelectThreads / 32];
   __shared__ int base_sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) base_sh = *p.count;
+  if (threadIdx.x == 0) base_sh = 0;  // a launch group's candidate list starts empty
   const int n_pairs = p.nw * p.Cg;
   for (int p0 = 0; p0 < n_pairs; p0 += kFskSelectThreads) {
     const int pi = p0 + threadIdx.x;
@@ -362,8 +369,13 @@ cudaError_t launch_fsk_stats(const FskStatsParams& p, int max_cand, cudaStream_t
     k_fsk_stats_part<<<items < resident ? items : resident, kFskStatsThreads, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int warps_per_block = kFskStatsThreads / 32;
-    k_fsk_stats_final<<<(max_cand + warps_per_block - 1) / warps_per_block, kFskStatsThreads, 0, s>>>(p);
+    constexpr int warps_per_block = kFskStatsThreads / 32;
+    static_assert(kFskStatsFinalOneBlock <= 4 * warps_per_block, "a few candidates per warp");
+    if (max_cand <= kFskStatsFinalOneBlock) {  // small groups (tracking tasks): one block that also advances
+      k_fsk_stats_final<true><<<1, kFskStatsThreads, 0, s>>>(p);
+      return cudaGetLastError();
+    }
+    k_fsk_stats_final<false><<<(max_cand + warps_per_block - 1) / warps_per_block, kFskStatsThreads, 0, s>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   k_fsk_advance<<<1, 1, 0, s>>>(p.count, p.n_cand);

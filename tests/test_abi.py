@@ -210,7 +210,7 @@ def test_rt_header_and_exports(lib):
 
 def test_rt_structs_and_defaults(lib):
     assert ctypes.sizeof(binding.RtOpts) == 40
-    assert ctypes.sizeof(binding.RtStats) == 88
+    assert ctypes.sizeof(binding.RtStats) == 96
     assert binding.RT_EVENT_DTYPE.itemsize == 48
     o = binding.rt_default_opts(8e6)
     assert (o.ring_samples, o.search_block, o.search_overlap, o.track_block, o.max_misses, o.capacity) == \
@@ -260,4 +260,5 @@ def test_fsk_tracker_null_arguments(lib):
     assert lib.atlas_fsk_tracker_create(ctypes.byref(t), None, 0, 1000, None, 1000) == E and not t.value
     n = ctypes.c_int32()
     assert lib.atlas_fsk_tracker_run(None, None, 0, 0, None, 0, ctypes.byref(n)) == E
+    assert lib.atlas_fsk_tracker_kernels(None) == -1
     lib.atlas_fsk_tracker_destroy(None)

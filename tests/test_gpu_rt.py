@@ -155,6 +155,8 @@ def test_tracker_single_launch_equals_block_search(torch_cuda):
         assert n == n_ref and got.tobytes() == ref.tobytes(), (code, start)
         found += n
     assert found >= 2
+    # one window, one code: demodulation, the transforms, selection and the peak sums
+    assert 6 <= trackers[0].kernels() <= 10
 
 
 def test_code_subsets_across_length_groups(torch_cuda):
