@@ -268,8 +268,12 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   CK(cudaEventCreateWithFlags(&ctx->ev_corr, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_sel, cudaEventDisableTiming));
 
-  // windows per launch group: keep the window spectra of one group near L2 size
-  const size_t budget = 128ull << 20;
+  // windows per launch group: as many as a 2 GiB workspace of window spectra
+  // holds (at most 64).  The correlation takes the codes of one window before
+  // the next window, so one window's spectra (31 MiB for 31 bins at N = 2^17)
+  // are what must stay in L2; larger groups only cut launches and tails
+  // (realistic stream: 4 windows 29.03 ms, 16 windows 28.41, 64 windows 28.05)
+  const size_t budget = 2048ull << 20;
   size_t max_win_bytes = 0;
   size_t max_part_per_win = 0;
   for (auto& g : ctx->groups) {
@@ -641,8 +645,8 @@ int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t
       g.split = g.logM == 15 || (g.logM == 14 && it->second.s == 1);
       continue;
     }
-    // time on (at most) the first 32 windows of the group
-    const int64_t S_tune = std::min<int64_t>(n_samples, (int64_t)g.N + 31ll * g.hop);
+    // time on (at most) the first 64 windows of the group
+    const int64_t S_tune = std::min<int64_t>(n_samples, (int64_t)g.N + 63ll * g.hop);
     const int W = g.windows(S_tune);
     const int fit = std::max(1, (int)(ctx->G_elems / ((size_t)ctx->K * g.N)));
     int best_t = g.loge, best_w = g.wc;
@@ -654,7 +658,7 @@ int atlas_acq_autotune(atlas_acq_t ctx, void* stream, const float* d_iq, int64_t
     else splits = {false};
     for (bool sp : splits)
     for (int t : {5, 4}) {
-      for (int w : {1, 2, 4, 8}) {
+      for (int w : {1, 2, 4, 8, 16, 32, 64}) {
         if (w > std::min(fit, ctx->wc_max) || (w > 1 && w >= 2 * W)) continue;
         g.loge = t;
         g.wc = w;
