@@ -571,7 +571,7 @@ def run_fsk(args, rank: int, world: int, dev, torch, dist) -> None:
     h_iq = torch.from_numpy(np.ascontiguousarray(w.iq16)).pin_memory()
     h_out = torch.empty(cap * rec, dtype=torch.uint8).pin_memory()
     h_cnt = torch.zeros(1, dtype=torch.int32).pin_memory()
-    for _ in range(2):
+    for _ in range(max(2, args.warmup)):
         s.run_host_ptr(st.cuda_stream, h_iq.data_ptr(), S, h_out.data_ptr(), cap, h_cnt.data_ptr())
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -827,7 +827,7 @@ def main() -> None:
     h_x = torch.from_numpy(wl.iq().copy()).pin_memory()
     h_out = torch.empty(cap * 32, dtype=torch.uint8).pin_memory()
     h_cnt = torch.zeros(1, dtype=torch.int32).pin_memory()
-    for _ in range(2):
+    for _ in range(max(2, args.warmup)):
         s.run_host_ptr(st.cuda_stream, h_x.data_ptr(), S, h_out.data_ptr(), cap, h_cnt.data_ptr())
     torch.cuda.synchronize(dev)
     if world > 1:
