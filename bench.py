@@ -386,9 +386,10 @@ def run_learned(args, rank: int, world: int, dev, torch, dist) -> None:
 def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
     """Reduced-precision row: the realistic workload with the per-code inverse
     transforms in FP32 (CUDA cores) and as FP16 / BF16 tensor-core contractions;
-    throughput, speedup over FP32, agreement of the detections with FP32, and
-    score / ToA error against the FP64 oracle on the injected tags' cells."""
-    from oracle import acq
+    throughput, speedup over FP32, agreement of the detections and scores with
+    the FP32 path, and the injected tags' cells found.  The errors against the
+    FP64 oracle are asserted by tests/test_gpu_precision.py."""
+    import math
     from paper_2005_10445_gb300 import binding
     wl = make_workload(2 + rank)
     S = wl.n_samples
@@ -422,21 +423,26 @@ def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
         srch.close()
     key = lambda d: (int(d["code"]), int(d["window"]), int(d["lag"]), int(d["freq_bin"]))
     ref = {key(d): d for d in dets[0]}
-    W, hop = acq.window_plan(S, wl.fft_len, len(wl.chips[0]) * wl.sps)
-    pairs = sorted({(min(int(t.delay) // hop, W - 1), t.code) for t in wl.tags})
-    ora, _ = acq.search(wl.x, wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len, pairs=pairs)
-    ob = {o.key(): o for o in ora}
+    # the injected tags' cells (integer delays, known bins) under the window rule
+    N, L = wl.fft_len, len(wl.chips[0]) * wl.sps
+    hop = N - L
+    W = max(1, math.ceil((S - N) / hop) + 1)
+    tag_cells = set()
+    for t in wl.tags:
+        w = min(int(t.delay) // hop, W - 1)
+        tag_cells.add((t.code, w, int(t.delay) - w * hop, t.bin))
     for prec in (0, 1, 2):
         got = {key(d): d for d in dets[prec]}
-        score_err = [abs(float(got[k]["score"]) / ob[k].score - 1) for k in ob if k in got]
-        toa_err = [abs(float(got[k]["toa"]) - ob[k].toa) for k in ob if k in got]
+        common = set(got) & set(ref)
+        score_diff = [abs(float(got[k]["score"]) / float(ref[k]["score"]) - 1) for k in common]
+        toa_diff = [abs(float(got[k]["toa"]) - float(ref[k]["toa"])) for k in common]
         res[prec].update({
             "speedup_vs_fp32": res[0]["ms_per_step"] / res[prec]["ms_per_step"],
-            "fp32_detections_reproduced": len(set(got) & set(ref)) / max(len(ref), 1),
+            "fp32_detections_reproduced": len(common) / max(len(ref), 1),
             "extra_vs_fp32": len(set(got) - set(ref)),
-            "oracle_tag_cells_found": sum(k in got for k in ob) / max(len(ob), 1),
-            "max_score_rel_err_vs_oracle": max(score_err or [0.0]),
-            "max_toa_err_vs_oracle": max(toa_err or [0.0])})
+            "tag_cells_found": len(tag_cells & set(got)) / max(len(tag_cells), 1),
+            "max_score_rel_diff_vs_fp32": max(score_diff or [0.0]),
+            "max_toa_diff_vs_fp32": max(toa_diff or [0.0])})
     if rank == 0:
         names = {0: "fp32", 1: "fp16-tc", 2: "bf16-tc"}
         line = {"metric": METRIC, "value": res[1]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -445,7 +451,7 @@ def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
                 "data": "synthetic",
                 "config": {"workload": "precision: " + WORKLOAD,
                            "l2": "flushed before each step (256 MiB write), outside the timed events",
-                           "oracle_cells": f"{len(pairs)} (window, code) pairs of the injected tags, all bins"},
+                           "tag_cells": f"{len(tag_cells)} (code, window, lag, bin) cells of the injected tags"},
                 "per_precision": {names[p]: r for p, r in res.items()}}
         print(json.dumps(line), flush=True)
 
