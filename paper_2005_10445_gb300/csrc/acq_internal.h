@@ -70,6 +70,11 @@ struct SelectParams {
   int capacity;
   int* count;               // running count (device)
   atlas_cell* cells;        // optional [Wmax][C][K]
+  // optional workspace of [nw * Cg] per-pair results: with it the pairs are
+  // evaluated by many blocks and then compacted in order by one (the same
+  // records as the single-block selection)
+  int* tmp_flags = nullptr;
+  atlas_detection* tmp_recs = nullptr;
 };
 
 // FP64 direct recompute at a-1, a, a+1 and parabolic refinement.
@@ -112,6 +117,7 @@ cudaError_t launch_window_fft_e5(int logM, bool split, const WindowFftParams& p,
 cudaError_t launch_corr_e4(int logM, bool split, const CorrParams& p, cudaStream_t s);
 cudaError_t launch_corr_e5(int logM, bool split, const CorrParams& p, cudaStream_t s);
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s);
+int select_launches(const SelectParams& p);  // kernels launch_select starts for p
 cudaError_t launch_pair_stats(const PairStatsParams& p, cudaStream_t s);
 cudaError_t launch_refine(const RefineParams& p, int grid, cudaStream_t s);
 cudaError_t prepare_kernels();  // raises the dynamic shared-memory limits once per process

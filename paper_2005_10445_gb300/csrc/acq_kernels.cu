@@ -27,9 +27,12 @@
 //                 the correlation never leaves the chip
 //   k_select      per (w, c): combine the sps partial results of each bin,
 //                 score = P_max / floor, best bin, threshold, ordered compaction
+//                 (one block; or k_select_pairs over many blocks into a
+//                 workspace, then k_select_compact in one)
 //   k_refine      per detection: direct |corr|^2 at a-1, a, a+1 (exact fixed-point
-//                 phase, FP32 rotation, FP64 accumulation) and the parabola
-//                 vertex in FP64 (Section 3 step 8, "interpolated")
+//                 phase, FP32 rotation, FP32 within a chip and FP64 across
+//                 chips) and the parabola vertex in FP64 (Section 3 step 8,
+//                 "interpolated")
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -181,6 +184,65 @@ __global__ void __launch_bounds__(kMixQ) k_mix(MixParams p) {
 
 constexpr int kSelectThreads = 512;  // one warp per (window, code) pair
 
+// One (window, code) pair by one warp: the best bin by score (ties keep the
+// smaller bin), its lag and peak; the per-cell statistics when asked.  The
+// result is valid in lane 0.
+__device__ __forceinline__ void select_pair(const SelectParams& p, int pi, int lane, int& flag,
+                                            atlas_detection& d) {
+  const int wl = pi / p.Cg, c = pi % p.Cg;
+  const int w = p.w0 + wl;
+  float bscore = -1.f, bpmax = 0.f;
+  int bk = 0x7fffffff, btau = 0;
+  for (int k = lane; k < p.K; k += 32) {
+    const float4* pr = p.part + (((int64_t)wl * p.Cg + c) * p.K + k) * p.sps;
+    float sum = 0.f, best = -1.f;
+    int bt = 0x7fffffff;
+    for (int r = 0; r < p.sps; ++r) {
+      const float4 v = pr[r];
+      sum += v.x;
+      better(best, bt, v.y, __float_as_int(v.z));
+    }
+    const float floor_ = sum / (float)p.N;
+    const float score = floor_ > 0.f ? best / floor_ : 0.f;
+    if (p.cells) {
+      atlas_cell cell;
+      cell.p_max = best;
+      cell.floor = floor_;
+      cell.lag = bt;
+      cell.valid = 1;
+      p.cells[((int64_t)w * p.C + p.codes[c]) * p.K + k] = cell;
+    }
+    if (score > bscore) {  // k increases along the loop: ties keep the smaller bin
+      bscore = score;
+      bk = k;
+      btau = bt;
+      bpmax = best;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, bscore, o);
+    const int k2 = __shfl_down_sync(0xffffffffu, bk, o);
+    const int t2 = __shfl_down_sync(0xffffffffu, btau, o);
+    const float p2 = __shfl_down_sync(0xffffffffu, bpmax, o);
+    if (s2 > bscore || (s2 == bscore && k2 < bk)) {
+      bscore = s2;
+      bk = k2;
+      btau = t2;
+      bpmax = p2;
+    }
+  }
+  flag = bscore >= p.threshold ? 1 : 0;
+  d.code = p.codes[c];
+  d.window = w;
+  d.lag = btau;
+  d.freq_bin = bk;
+  d.score = bscore;
+  d.peak_power = bpmax;
+  d.toa = 0.0;
+}
+
+// Single block: rounds of one pair per warp, compacted in order by thread 0.
 __global__ void __launch_bounds__(kSelectThreads) k_select(SelectParams p) {
   __shared__ int flags[kSelectThreads / 32];
   __shared__ atlas_detection recs[kSelectThreads / 32];
@@ -192,61 +254,9 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(SelectParams p) {
     const int pi = p0 + warp;
     int flag = 0;
     if (pi < n_pairs) {
-      const int wl = pi / p.Cg, c = pi % p.Cg;
-      const int w = p.w0 + wl;
-      float bscore = -1.f, bpmax = 0.f;
-      int bk = 0x7fffffff, btau = 0;
-      for (int k = lane; k < p.K; k += 32) {
-        const float4* pr = p.part + (((int64_t)wl * p.Cg + c) * p.K + k) * p.sps;
-        float sum = 0.f, best = -1.f;
-        int bt = 0x7fffffff;
-        for (int r = 0; r < p.sps; ++r) {
-          const float4 v = pr[r];
-          sum += v.x;
-          better(best, bt, v.y, __float_as_int(v.z));
-        }
-        const float floor_ = sum / (float)p.N;
-        const float score = floor_ > 0.f ? best / floor_ : 0.f;
-        if (p.cells) {
-          atlas_cell cell;
-          cell.p_max = best;
-          cell.floor = floor_;
-          cell.lag = bt;
-          cell.valid = 1;
-          p.cells[((int64_t)w * p.C + p.codes[c]) * p.K + k] = cell;
-        }
-        if (score > bscore) {  // k increases along the loop: ties keep the smaller bin
-          bscore = score;
-          bk = k;
-          btau = bt;
-          bpmax = best;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float s2 = __shfl_down_sync(0xffffffffu, bscore, o);
-        const int k2 = __shfl_down_sync(0xffffffffu, bk, o);
-        const int t2 = __shfl_down_sync(0xffffffffu, btau, o);
-        const float p2 = __shfl_down_sync(0xffffffffu, bpmax, o);
-        if (s2 > bscore || (s2 == bscore && k2 < bk)) {
-          bscore = s2;
-          bk = k2;
-          btau = t2;
-          bpmax = p2;
-        }
-      }
-      if (lane == 0) {
-        flag = bscore >= p.threshold ? 1 : 0;
-        atlas_detection d;
-        d.code = p.codes[c];
-        d.window = w;
-        d.lag = btau;
-        d.freq_bin = bk;
-        d.score = bscore;
-        d.peak_power = bpmax;
-        d.toa = 0.0;
-        recs[warp] = d;
-      }
+      atlas_detection d;
+      select_pair(p, pi, lane, flag, d);
+      if (lane == 0) recs[warp] = d;
     }
     if (lane == 0) flags[warp] = flag;
     __syncthreads();
@@ -260,6 +270,60 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(SelectParams p) {
       }
       base_sh = n;
     }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *p.count = base_sh;
+}
+
+// Many blocks: one pair per warp into the workspace.
+__global__ void __launch_bounds__(kSelectThreads) k_select_pairs(SelectParams p) {
+  const int lane = threadIdx.x & 31;
+  const int pi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (pi >= p.nw * p.Cg) return;  // whole warps leave together
+  int flag = 0;
+  atlas_detection d;
+  select_pair(p, pi, lane, flag, d);
+  if (lane == 0) {
+    p.tmp_flags[pi] = flag;
+    p.tmp_recs[pi] = d;
+  }
+}
+
+// One block: the flagged pairs appended in pair order after the running
+// count, by a block-wide exclusive prefix sum per round of kCompactThreads.
+constexpr int kCompactThreads = 1024;
+
+__global__ void __launch_bounds__(kCompactThreads) k_select_compact(SelectParams p) {
+  __shared__ int warp_tot[kCompactThreads / 32];
+  __shared__ int base_sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base_sh = *p.count;
+  const int n_pairs = p.nw * p.Cg;
+  for (int p0 = 0; p0 < n_pairs; p0 += kCompactThreads) {
+    const int pi = p0 + threadIdx.x;
+    const int flag = pi < n_pairs ? p.tmp_flags[pi] : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    const int in_warp = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    if (warp == 0) {
+      const int v = warp_tot[lane];
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      warp_tot[lane] = x - v;  // exclusive
+    }
+    __syncthreads();
+    const int base = base_sh;
+    if (flag) {
+      const int idx = base + warp_tot[warp] + in_warp;
+      if (idx < p.capacity) p.out[idx] = p.tmp_recs[pi];
+    }
+    __syncthreads();  // every thread has read base_sh and warp_tot
+    if (threadIdx.x == kCompactThreads - 1) base_sh = base + warp_tot[warp] + in_warp + flag;
     __syncthreads();
   }
   if (threadIdx.x == 0) *p.count = base_sh;
@@ -453,8 +517,21 @@ cudaError_t launch_corr(int logM, int loge, bool split, const CorrParams& p, cud
 }
 
 cudaError_t launch_select(const SelectParams& p, cudaStream_t s) {
+  const int n_pairs = p.nw * p.Cg;
+  constexpr int warps = kSelectThreads / 32;
+  if (p.tmp_flags && p.tmp_recs && n_pairs > warps) {
+    k_select_pairs<<<(n_pairs + warps - 1) / warps, kSelectThreads, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_select_compact<<<1, kCompactThreads, 0, s>>>(p);
+    return cudaGetLastError();
+  }
   k_select<<<1, kSelectThreads, 0, s>>>(p);
   return cudaGetLastError();
+}
+
+int select_launches(const SelectParams& p) {
+  return (p.tmp_flags && p.tmp_recs && p.nw * p.Cg > kSelectThreads / 32) ? 2 : 1;
 }
 
 cudaError_t launch_pair_stats(const PairStatsParams& p, cudaStream_t s) {

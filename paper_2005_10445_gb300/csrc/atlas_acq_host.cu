@@ -104,6 +104,9 @@ struct atlas_acq_ctx {
   size_t G_elems = 0;
   float4* d_part = nullptr;
   size_t part_elems = 0;
+  // per-pair selection results of one launch group (the many-block selection)
+  int* d_sel_flags = nullptr;
+  atlas_detection* d_sel_recs = nullptr;
   int* d_status = nullptr;
   // the selection of a launch group runs on a side stream, overlapping the next
   // group's mix and window transforms (its partial results are read before the
@@ -179,6 +182,8 @@ void free_ctx(atlas_acq_ctx* ctx) {
   cudaFree(ctx->d_inc);
   cudaFree(ctx->d_G);
   cudaFree(ctx->d_part);
+  cudaFree(ctx->d_sel_flags);
+  cudaFree(ctx->d_sel_recs);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_stage_out);
@@ -276,9 +281,11 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   const size_t budget = 2048ull << 20;
   size_t max_win_bytes = 0;
   size_t max_part_per_win = 0;
+  size_t max_codes = 0;
   for (auto& g : ctx->groups) {
     max_win_bytes = std::max(max_win_bytes, (size_t)n_freq * g.N * sizeof(float2));
     max_part_per_win = std::max(max_part_per_win, (size_t)g.codes.size() * n_freq * sps * 2);
+    max_codes = std::max(max_codes, g.codes.size());
   }
   int wc = o.windows_per_launch > 0 ? o.windows_per_launch : (int)std::max<size_t>(1, budget / max_win_bytes);
   wc = std::min(wc, 64);
@@ -287,6 +294,10 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
   ctx->part_elems = (size_t)wc * max_part_per_win;
   if (cudaMalloc((void**)&ctx->d_G, ctx->G_elems * sizeof(float2)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
   if (cudaMalloc((void**)&ctx->d_part, ctx->part_elems * sizeof(float4)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
+  const size_t sel_pairs = (size_t)wc * max_codes;
+  if (cudaMalloc((void**)&ctx->d_sel_flags, sel_pairs * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&ctx->d_sel_recs, sel_pairs * sizeof(atlas_detection)) != cudaSuccess)
+    return ATLAS_ERR_NO_MEMORY;
 
   // twiddle tables and code banks
   auto tables = [&](int lm, const float2** dst) -> int {
@@ -411,12 +422,14 @@ int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const floa
   c.capacity = capacity;
   c.count = d_count;
   c.cells = cells;
+  c.tmp_flags = ctx->d_sel_flags;  // the selections of a context run in order on its side stream
+  c.tmp_recs = ctx->d_sel_recs;
   CK(cudaEventRecord(ctx->ev_corr, st));
   CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_corr, 0));
   CK(atlas::launch_select(c, ctx->aux));
   CK(cudaEventRecord(ctx->ev_sel, ctx->aux));
   sel_pending = true;
-  if (profiling) ctx->prof_launches += 1;
+  if (profiling) ctx->prof_launches += atlas::select_launches(c);
   return ATLAS_OK;
 }
 
