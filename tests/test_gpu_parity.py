@@ -201,6 +201,18 @@ def test_windows_per_launch_does_not_change_results(torch_cuda):
     assert na == nb and a.tobytes() == b.tobytes() and ca.tobytes() == cb.tobytes()
 
 
+def test_selection_forms_agree(torch_cuda):
+    """Launch groups of one window (pairs selected by the one-block kernel)
+    and of every window (the many-block kernel and the ordered compaction):
+    the same records in (window, code) order, at threshold 0 (every pair)."""
+    wl = synth.small(seed=14)
+    _, a, na, _ = gpu_search(torch_cuda, wl, threshold=0.0, windows_per_launch=1)
+    _, b, nb, _ = gpu_search(torch_cuda, wl, threshold=0.0)
+    assert na == nb > 16 and a.tobytes() == b.tobytes()
+    keys = [(int(d["window"]), int(d["code"])) for d in b]
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+
+
 def test_short_stream_rejected(torch_cuda):
     from paper_2005_10445_gb300.binding import AtlasError, Search
     wl = synth.small()
