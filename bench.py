@@ -213,7 +213,7 @@ def unfused_baseline(args, wl, x, st, flush, dev, torch, fused_value):
     return {"value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps, "detections_per_step": n,
             "fused_speedup": fused_value / value,
             "pipeline": "paper-organised: mix kernel, cuFFT forward (windows x bins), multiply kernel for every "
-                        "code, cuFFT inverse in place (4 windows x 16 codes x 31 bins per group, the surface in "
+                        "code, cuFFT inverse in place (16 windows x 16 codes x 31 bins per group, the surface in "
                         "HBM), power/floor/argmax kernel reading the surface; same selection and refinement"}
 
 

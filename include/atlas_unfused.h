@@ -31,8 +31,8 @@ typedef struct atlas_unfused* atlas_unfused_t;
  * chips, chips_per_code (all equal), n_codes, samples_per_chip, fs_hz,
  * freq_offsets_hz, n_freq: as atlas_acq_create.  fft_len: N (0 = 2 nextpow2(L)),
  * a power of two with N > L.  threshold: on P_max / floor.
- * windows_per_launch: windows per launch group (the surface of one group,
- * windows x codes x bins x N complex values, is held in device memory).
+ * windows_per_launch: windows per launch group, 0 = 16 (the surface of one
+ * group, windows x codes x bins x N complex values, is held in device memory).
  * Builds the full N-point code spectra with cuFFT and plans the transforms.
  */
 int atlas_unfused_create(atlas_unfused_t* out, const int8_t* chips, const int32_t* chips_per_code,

@@ -171,7 +171,9 @@ int create_impl(atlas_unfused* u, const int8_t* chips, const int32_t* cpc, int32
   u->N = fft_len ? fft_len : 2 << lg;
   if ((u->N & (u->N - 1)) != 0 || u->N <= u->L || u->N > (1 << 24)) return ATLAS_ERR_UNSUPPORTED;
   u->hop = u->N - u->L;
-  u->wc = wpl > 0 ? wpl : 4;
+  // 16 windows by default (an 8 GiB surface for 16 codes x 31 bins at N = 2^17):
+  // larger cuFFT batches measured faster (78.7, 79.5, 79.9 Msamples/s at 4, 8, 16)
+  u->wc = wpl > 0 ? wpl : 16;
   const int C = u->C, K = u->K, N = u->N;
   std::vector<int64_t> off(C);
   std::vector<int> nch(C, u->n_chips), hop(C, u->hop), codes(C);
