@@ -202,6 +202,16 @@ def lag_sums(x: np.ndarray, g1: np.ndarray, g0: np.ndarray, dc: np.ndarray,
     return cm, c0, cp, q, p
 
 
+def interp_offset(cm: float, c0: float, cp: float, a: int, S: int, n_c: int) -> float:
+    """Sub-sample offset of the peak at absolute lag a (step 8, "interpolated"):
+    the parabola vertex through the squared correlations at a-1, a, a+1, and 0
+    at the stream ends, where a neighbour lag is not a searched lag
+    (a-1 < 0 or a+1 > S - n_c)."""
+    if a - 1 < 0 or a + 1 > S - n_c:
+        return 0.0
+    return acq.parabolic_offset(cm * cm, c0 * c0, cp * cp)
+
+
 @dataclasses.dataclass
 class FskDetection:
     code: int
@@ -272,8 +282,6 @@ def search_samples(x: np.ndarray, chips_list: Sequence[np.ndarray], sps: int, fs
         if score >= threshold:
             a = w * hop + j
             cm, c0, cp, q, p = lag_sums(x, g1, g0, dcs[c], a)
-            delta = 0.0
-            if a - 1 >= 0 and a + 1 <= S - n_c:
-                delta = acq.parabolic_offset(cm * cm, c0 * c0, cp * cp)
+            delta = interp_offset(cm, c0, cp, a, S, n_c)
             dets.append(FskDetection(c, w, j, score, a + delta, c0, q, p))
     return dets, cells

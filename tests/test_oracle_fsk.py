@@ -196,6 +196,39 @@ def test_noise_free_tag_closed_forms(f_lo, delay):
     assert abs(d.toa - delay) <= 0.5
 
 
+def test_stream_end_offset_golden():
+    """The interpolation offset is 0 when a neighbour of the peak lies past the
+    last searched lag S - n_c (tests/golden/refine_stream_end.txt: correlation
+    values -1.5, 3, -2 at lags 4, 5, 6 of an 8-sample stream, n_c = 3)."""
+    g = _fixture("refine_stream_end.txt")
+    cm, c0, cp = g["upper_corr"]
+    assert fsk.interp_offset(cm, c0, cp, 5, 8, 3) == 0.0
+    assert fsk.interp_offset(cm, c0, cp, 0, 8, 3) == 0.0
+    assert fsk.interp_offset(cm, c0, cp, 4, 8, 3) == pytest.approx(g["interior_delta"][0], rel=1e-15)
+
+
+def test_peak_at_the_last_lag_is_not_interpolated():
+    """A tag whose peak is the stream's last searched lag a = S - n_c (the last
+    window's last valid lag, Section 2.1): toa = a exactly.  The seeded noise
+    makes the two neighbours unequal, so ignoring the stream end would move it."""
+    S = 20000
+    x, chips, sps, fs, f1, f0, h = _noise_free(0.0, 0, S=S)
+    g1, g0 = fsk.filters(h, f1, f0, sps, fs)
+    n_c = len(chips) * sps + g1.shape[0] - 1
+    a = S - n_c
+    x, *_ = _noise_free(0.0, a, S=S)
+    rng = np.random.default_rng(31)
+    x = x + 20.0 * (rng.standard_normal(S) + 1j * rng.standard_normal(S))
+    dets, _ = fsk.search_samples(x, [chips], sps, fs, f1, f0, 0.0, h, threshold=10.0)
+    N, W, hop, _ = fsk.plan(S, len(chips), sps, g1.shape[0])
+    hit = [d for d in dets if d.window * hop + d.lag == a]
+    assert len(hit) == 1 and hit[0].window == W - 1
+    assert hit[0].toa == float(a)
+    cm, c0, cp, _, _ = fsk.lag_sums(fsk.lo_mix(x, 0.0, fs), g1, g0,
+                                    fsk.code_demod(chips, sps, f1, f0, fs, g1, g0)[0], a)
+    assert abs(acq.parabolic_offset(cm * cm, c0 * c0, cp * cp)) > 1e-6
+
+
 def test_noisy_sums_obey_cauchy_schwarz():
     w = synth.fsk_small(seed=8)
     dets, _ = fsk.search(w.iq16, w.chips, w.sps, w.fs_hz, w.f1_hz, w.f0_hz, w.f_lo_hz, w.h_bp)
@@ -328,6 +361,11 @@ def _mutants():
         j = int(np.argmax(P[:nv]))
         return float(P[j]), j, float(P[:nv].mean())
 
+    def no_upper_stream_end(cm, c0, cp, a, S, n_c):
+        if a - 1 < 0:
+            return 0.0
+        return acq.parabolic_offset(cm * cm, c0 * c0, cp * cp)
+
     def q_of_the_code(x, g1, g0, dc, a):
         cm, c0, cp, q, p = fsk_lag_sums(x, g1, g0, dc, a)
         return cm, c0, cp, float(np.dot(dc, dc)), p
@@ -335,7 +373,7 @@ def _mutants():
     return [("demod_values", typo_denominator), ("chip_filter", unreversed_chip_filter),
             ("lo_mix", lo_plus), ("replica", phase_reset_per_chip),
             ("corr_fft", convolution_not_correlation), ("cell_stats", floor_valid_only),
-            ("lag_sums", q_of_the_code)]
+            ("lag_sums", q_of_the_code), ("interp_offset", no_upper_stream_end)]
 
 
 fsk_lag_sums = fsk.lag_sums
@@ -347,7 +385,9 @@ PINS = [test_hand_worked_example,
         test_correlation_of_shifted_code_peaks_at_the_shift,
         test_floor_by_parseval,
         test_noisy_sums_obey_cauchy_schwarz,
-        test_brute_force_tiny_search]
+        test_brute_force_tiny_search,
+        test_stream_end_offset_golden,
+        test_peak_at_the_last_lag_is_not_interpolated]
 
 
 @pytest.mark.parametrize("name,fn", _mutants(), ids=[f"{n}:{f.__name__}" for n, f in _mutants()])

@@ -52,6 +52,51 @@ def test_hand_worked_example():
     assert d.peak_power == pytest.approx(g["peak_power"][0], rel=1e-12)
 
 
+# --- bin selection ties (tests/golden/select_ties.txt) ----------------------
+
+def test_select_ties_golden():
+    g = _read_fixture("select_ties.txt")
+    for case in "abc":
+        v = g["case_" + case]
+        cells = [acq.Cell(v[i], int(v[i + 1]), v[i + 2]) for i in range(0, len(v), 3)]
+        k, s = acq.select(cells)
+        want_k, want_s = g["want_" + case]
+        assert k == int(want_k), case
+        assert s == want_s, case
+
+
+def test_duplicated_bins_select_the_first():
+    """Two identical frequencies give identical cells; the search reports the
+    smaller bin index (the hand-worked example's detection, at bin 0 of 2)."""
+    g = _read_fixture("hand_worked_example.txt")
+    chips = np.array(g["chips"], dtype=np.int8)
+    x = np.array(g["x_re"]) + 1j * np.array(g["x_im"])
+    dets, cells = acq.search(x, [chips], 1, g["fs"][0], [0.0, 0.0], fft_len=int(g["N"][0]), threshold=2.0,
+                             keep_cells=True)
+    assert len(dets) == 1 and dets[0].freq_bin == 0
+    assert cells[(0, 0)][0] == cells[(0, 0)][1]
+
+
+# --- refinement at the stream ends (tests/golden/refine_stream_end.txt) ------
+
+def test_refine_stream_ends_golden():
+    g = _read_fixture("refine_stream_end.txt")
+    N, fs = int(g["N"][0]), g["fs"][0]
+    chips = np.array(g["chips"], dtype=np.int8)
+    for end in ("upper", "lower"):
+        x = np.array(g[end + "_x"], dtype=np.complex128)
+        dets, _ = acq.search(x, [chips], 1, fs, g["freqs"], fft_len=N, threshold=1.0)
+        assert len(dets) == 1, end
+        d = dets[0]
+        assert d.lag == int(g[end + "_lag"][0]), end
+        assert d.toa == g[end + "_toa"][0], end
+    x = np.array(g["upper_x"], dtype=np.complex128)
+    d = acq.search(x, [chips], 1, fs, g["freqs"], fft_len=N, threshold=1.0)[0][0]
+    assert d.score == pytest.approx(g["upper_score"][0], rel=1e-15)
+    assert d.peak_power == pytest.approx(g["upper_peak_power"][0], rel=1e-15)
+    assert acq.parabolic_offset(*g["interior_p"]) == pytest.approx(g["interior_delta"][0], rel=1e-15)
+
+
 # --- windowing: every start lag searched exactly once (Section 2.1) --------
 
 @pytest.mark.parametrize("S,N,L", [(16384, 16384, 2046), (8_000_000, 131072, 65536), (40000, 8192, 2400),
@@ -343,16 +388,34 @@ def _mutants():
             return 0.0
         return min(0.5, max(-0.5, 0.5 * (pp - pm) / den))
 
+    def larger_bin_on_ties(cells):
+        best_k, best_s = 0, -1.0
+        for k, c in enumerate(cells):
+            s = c.p_max / c.floor if c.floor > 0 else 0.0
+            if s >= best_s:
+                best_k, best_s = k, s
+        return best_k, best_s
+
+    def no_upper_stream_end(x, chips, sps, f_hz, fs_hz, a):
+        p0 = acq.direct_power(x, chips, sps, f_hz, fs_hz, a)
+        if a - 1 < 0:
+            return float(a), p0
+        pm = acq.direct_power(x, chips, sps, f_hz, fs_hz, a - 1)
+        pp = acq.direct_power(x, chips, sps, f_hz, fs_hz, a + 1)
+        return float(a) + acq.parabolic_offset(pm, p0, pp), p0
+
     return [("corr_fft", no_conj), ("mix", mix_plus), ("cell_stats", floor_valid_only),
             ("cell_stats", last_tie), ("replica", drop_last_chip),
-            ("parabolic_offset", sign_flipped_vertex)]
+            ("parabolic_offset", sign_flipped_vertex), ("select", larger_bin_on_ties),
+            ("refine", no_upper_stream_end)]
 
 
 PINS = [test_hand_worked_example,
         lambda: test_delta_input_gives_reversed_code(1250.0),
         test_tag_on_bin_closed_form_power, test_parseval_floor,
         test_autocorrelation_peak_equals_code_length, test_brute_force_tiny_search,
-        lambda: test_parabolic_vertex_exact(0.12), test_fractional_delay_toa_direction]
+        lambda: test_parabolic_vertex_exact(0.12), test_fractional_delay_toa_direction,
+        test_select_ties_golden, test_duplicated_bins_select_the_first, test_refine_stream_ends_golden]
 
 
 @pytest.mark.parametrize("name,fn", _mutants(), ids=[f"{n}:{f.__name__}" for n, f in _mutants()])
