@@ -46,7 +46,9 @@ enum {
   ATLAS_ERR_CUDA = -2,         /* a CUDA runtime call failed; see atlas_acq_last_error() */
   ATLAS_ERR_NO_MEMORY = -3,    /* device or host allocation failed (create time only) */
   ATLAS_ERR_UNSUPPORTED = -4,  /* a size outside what the kernels support (see atlas_acq_create) */
-  ATLAS_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+  ATLAS_ERR_TIMEOUT = -5,      /* reserved for a bounded device-side wait that gives up; no kernel of
+                                  this library waits on another block, stream or device, so no call
+                                  returns it at present */
   ATLAS_ERR_DEVICE = -6        /* a kernel reported an internal check failure (device status word) */
 };
 
@@ -313,21 +315,26 @@ int atlas_acq_profile_end(atlas_acq_t ctx, atlas_acq_profile* out);
  * that must not grow the process's footprint, or a real-time loop that cannot
  * afford an allocation's implicit synchronisation.
  *   stream, d_iq, n_samples, d_out, capacity, d_count  as in atlas_acq_run
- *   d_chips        device, [n_chips] +/-1 int8 chips of the one code (caller-owned)
+ *   d_chips        device, [n_chips] +/-1 int8 chips of the one code (caller-owned).
+ *                  They are not checked (they are device memory): other values
+ *                  give scores that do not match atlas_acq_run.
  *   samples_per_chip, fs_hz  as in atlas_acq_create
  *   freq_offsets_hz  host, [n_freq] carrier offsets in Hz (read during the call)
  *   fft_len        N; 0 = 2 * nextpow2(n_chips * samples_per_chip)
  *   threshold      detection threshold on P_max / floor
- * All intermediate arrays live in one static device array of about 4.3 MiB
- * that each GPU loading the library keeps until the process exits.  Limits:
- * N <= 16384, n_freq <= 32, samples_per_chip a power of two <= 16,
- * N / samples_per_chip >= 1024; beyond them the call returns
- * ATLAS_ERR_UNSUPPORTED and does no device work.  The first call on a device
- * looks up the array's device address (and sets kernel attributes); make that
- * first call before any stream capture.  Every call reuses the same array and
- * rewrites what it reads; calls whose device work may overlap (other host
- * threads, or streams not ordered with this one) race on it.  Results match
- * atlas_acq_run for the same code; the call is asynchronous on `stream`.
+ * All intermediate arrays live in one static device array of 4,342,016 bytes
+ * (about 4.14 MiB).  A GPU holds it from the time the library's device code
+ * is loaded there (with CUDA's lazy module loading, the first call on that
+ * device) until the process exits.  Limits: N <= 16384, n_freq <= 32,
+ * samples_per_chip a power of two <= 16, N / samples_per_chip >= 1024; beyond
+ * them the call returns ATLAS_ERR_UNSUPPORTED and does no device work.  A
+ * stream longer than atlas_acq_run accepts (8 * INT32_MAX samples) returns
+ * ATLAS_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (and sets kernel attributes); make that first call before
+ * any stream capture.  Every call reuses the same array and rewrites what it
+ * reads; calls whose device work may overlap (other host threads, or streams
+ * not ordered with this one) race on it.  The records equal atlas_acq_run's
+ * for the same code bit for bit; the call is asynchronous on `stream`.
  */
 int atlas_acq_run_static(void* stream, const float* d_iq, int64_t n_samples, const int8_t* d_chips,
                          int32_t n_chips, int32_t samples_per_chip, double fs_hz,

@@ -10,12 +10,20 @@
 // output buffers; every intermediate array of the search (twiddle tables,
 // phase increments, the code spectrum, one window's spectra and the
 // per-phase partial results) lives in one file-scope static device array,
-// g_scratch, of kStaticBytes bytes (about 4.3 MiB), which every GPU that
-// loads the library holds until the process exits.
+// g_scratch, of kStaticBytes = 4,342,016 bytes (about 4.14 MiB).  A GPU holds
+// it from the moment the library's device code is loaded there (with CUDA's
+// lazy module loading, the first call on that device) until the process exits.
 //
 // Limits: one code, N = fft_len <= 16384, at most 32 frequency bins,
-// samples_per_chip a power of two <= 16, N / samples_per_chip >= 1024.  Larger
-// sizes return ATLAS_ERR_UNSUPPORTED before any device work.
+// samples_per_chip a power of two <= 16, N / samples_per_chip >= 1024, and the
+// stream bound of atlas_acq_run (n_samples <= 8 * INT32_MAX).  Larger sizes
+// return ATLAS_ERR_UNSUPPORTED (ATLAS_ERR_INVALID_ARG for the stream length)
+// before any device work.  The chips are device memory and are not checked:
+// values other than +1 / -1 give scores that do not match atlas_acq_run.
+//
+// The twiddle tables and phase increments are computed on the host by the
+// same functions as the context path's and handed to the set-up kernel as a
+// parameter, so the records equal atlas_acq_run's bit for bit.
 //
 // Every call uses the same array and leaves its contents behind; a call
 // rewrites every region it reads before reading it.  Calls whose device work
@@ -29,6 +37,7 @@
 
 #include "acq_internal.h"
 #include "atlas_acq.h"
+#include "host_util.h"
 
 namespace atlas {
 namespace {
@@ -53,10 +62,14 @@ struct StaticMeta {
   int code;
 };
 
+constexpr int kStaticMaxTw = 256;  // table entries for M <= 2^14: 2^7 + 2^7
+
 struct StaticSetup {
   uint64_t inc[kStaticMaxBins];
-  int K, logM, n_chips, hop;
+  float2 tw[kStaticMaxTw];
+  int K, n_tw, n_chips, hop;
 };
+static_assert(sizeof(StaticSetup) <= 4096, "kernel parameter block");
 
 }  // namespace
 
@@ -65,8 +78,8 @@ static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
 namespace {
 
 // Writes the small per-call tables into g_scratch: phase increments, the
-// code's bookkeeping for the refinement kernel, and W_M^t twiddle tables
-// (W = exp(-2 pi i / M), high table then low table, FP64 then rounded).
+// code's bookkeeping for the refinement kernel, and the W_M^t twiddle tables
+// (high table then low table) that the host computed.
 __global__ void k_static_setup(StaticSetup s) {
   uint64_t* inc = reinterpret_cast<uint64_t*>(g_scratch + kOffInc);
   StaticMeta* meta = reinterpret_cast<StaticMeta*>(g_scratch + kOffMeta);
@@ -78,15 +91,7 @@ __global__ void k_static_setup(StaticSetup s) {
     meta->hop = s.hop;
     meta->code = 0;
   }
-  const int LB = s.logM / 2, HB = s.logM - LB;
-  const int nlo = 1 << LB, nhi = 1 << HB;
-  const double inv_m = 1.0 / (double)(1 << s.logM);
-  for (int i = threadIdx.x; i < nhi + nlo; i += blockDim.x) {
-    const double t = i < nhi ? (double)((int64_t)i << LB) : (double)(i - nhi);
-    double sn, cs;
-    sincospi(-2.0 * t * inv_m, &sn, &cs);
-    tw[i] = make_float2((float)cs, (float)sn);
-  }
+  for (int i = threadIdx.x; i < s.n_tw; i += blockDim.x) tw[i] = s.tw[i];
 }
 
 std::mutex g_mutex;
@@ -97,13 +102,6 @@ int ilog2(int64_t v) {
   int r = 0;
   while ((1ll << r) < v) ++r;
   return r;
-}
-
-uint64_t phase_increment(double f_hz, double fs_hz) {
-  double t = f_hz / fs_hz;
-  t -= nearbyint(t);
-  if (t >= 0.5) t -= 1.0;
-  return (uint64_t)(int64_t)llrint(ldexp(t, 64));
 }
 
 // Device address of g_scratch on the current device, looked up once per device.
@@ -150,7 +148,10 @@ extern "C" int atlas_acq_run_static(void* stream, const float* d_iq, int64_t n_s
   const int M = (int)(N / sps);
   const int logM = ilog2(M);
   const int hop = (int)(N - L);
-  const int W = n_samples <= N ? 1 : (int)((n_samples - N + hop - 1) / hop) + 1;
+  if (n_samples > (int64_t)INT32_MAX * 8) return ATLAS_ERR_INVALID_ARG;  // atlas_acq_run's stream bound
+  const int64_t W64 = n_samples <= N ? 1 : (n_samples - N + hop - 1) / hop + 1;
+  if (W64 > INT32_MAX) return ATLAS_ERR_UNSUPPORTED;
+  const int W = (int)W64;
 
   unsigned char* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return ATLAS_ERR_CUDA;
@@ -165,8 +166,11 @@ extern "C" int atlas_acq_run_static(void* stream, const float* d_iq, int64_t n_s
 
   StaticSetup su;
   for (int k = 0; k < kStaticMaxBins; ++k) su.inc[k] = k < n_freq ? phase_increment(freq_offsets_hz[k], fs_hz) : 0;
+  const std::vector<float2> tables = twiddle_tables(logM);
+  if (tables.size() > (size_t)kStaticMaxTw) return ATLAS_ERR_UNSUPPORTED;
+  for (int i = 0; i < kStaticMaxTw; ++i) su.tw[i] = i < (int)tables.size() ? tables[i] : make_float2(0.f, 0.f);
+  su.n_tw = (int)tables.size();
   su.K = n_freq;
-  su.logM = logM;
   su.n_chips = n_chips;
   su.hop = hop;
   k_static_setup<<<1, 256, 0, st>>>(su);

@@ -6,7 +6,7 @@ import pytest
 from oracle import acq
 from paper_2005_10445_gb300 import synth
 
-from test_gpu_parity import compare_detections
+from test_gpu_parity import compare_all_cells, compare_detections, near_tie_ok
 
 pytestmark = pytest.mark.gpu
 
@@ -131,3 +131,35 @@ def test_batch_full_size_sampled(torch_cuda):
         sel = np.array([d for d in got if (int(d["window"]), int(d["code"])) in pairs], dtype=got.dtype)
         compare_detections(sel, ora)
     b.close()
+
+
+def test_batch_stream_all_pairs(torch_cuda):
+    """One stream of the full batching workload (stream 7: 5.3 M samples at
+    4 MS/s, 64 codes of 2048-16384 chips in four length groups, 15 bins): the
+    batch graph's records equal the stream's own run, and the oracle (on every
+    host core) searches all of its (window, code) pairs; every detection and
+    every cell is compared."""
+    torch = torch_cuda
+    from oracle import parallel
+    from paper_2005_10445_gb300.binding import DETECTION_DTYPE, Batch, Search
+    wls = synth.batch()
+    i = 7
+    w = wls[i]
+    cap = 4096
+    searches = [Search(v.chips, v.sps, v.fs_hz, v.freqs_hz) for v in wls]
+    xs = [torch.from_numpy(v.iq().copy()).cuda() for v in wls]
+    out = torch.zeros(len(wls) * cap * 32, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(len(wls), dtype=torch.int32, device="cuda")
+    b = Batch(searches, [x.data_ptr() for x in xs], [v.n_samples for v in wls], out.data_ptr(), cap, cnt.data_ptr())
+    st = torch.cuda.current_stream()
+    b.run(st.cuda_stream)
+    st.synchronize()
+    got = out.cpu().numpy().view(DETECTION_DTYPE).reshape(len(wls), cap)[i, :min(int(cnt[i].item()), cap)].copy()
+    b.close()
+    ref, n_ref, cells = searches[i].run(xs[i], capacity=cap, cells=True)
+    assert got.tobytes() == ref.tobytes() and len(got) == n_ref
+    ora, ora_cells, procs = parallel.search(w.x, w.chips, w.sps, w.fs_hz, w.freqs_hz, 0)
+    assert len(ora_cells) == len(parallel.all_pairs(w.n_samples, w.chips, w.sps))
+    compare_detections(got, ora)
+    near_tie_ok(w, compare_all_cells(w, cells, ora_cells))
+    print(f"batch stream {i}: {len(ora)} detections over {len(ora_cells)} pairs, oracle on {procs} processes")

@@ -8,9 +8,15 @@ Bar:
   (the quotient's sensitivity), plus 1e-6 absolute;
 * detections: (code, window, lag) identical; score within 1e-4 relative; the
   FP64 peak sums w_c, q, p_c within 1e-4 relative (FP32 d against FP64 d);
-  arrival time within 2e-3 samples (the parabola's sensitivity to relative
-  errors of 1e-6 in the three correlation values, with a peak of width about
-  one chip).
+  arrival time within 1e-3 samples, the bar of the coherent search.  The
+  parabola's offset moves by about (sps / 4) sqrt(2) rho / sqrt(score) for a
+  relative error rho of d (correlation errors are a fixed fraction rho of
+  sqrt(floor); the peak is c0 = sqrt(score floor) with a mainlobe one chip
+  wide), far inside 1e-3 for rho near 1e-6.
+* cells searched below the default threshold (tests that lower it): the same
+  absolute correlation error is a larger fraction of a smaller peak, so the
+  score, w_c, p_c and ToA bars widen by sqrt(49 / score), the ratio of the
+  peak at the default threshold to the peak at the cell's score.
 """
 import numpy as np
 import pytest
@@ -22,7 +28,8 @@ pytestmark = pytest.mark.gpu
 
 SCORE_RTOL = 1e-4
 SUM_RTOL = 1e-4
-TOA_ATOL = 2e-3
+TOA_ATOL = 1e-3
+MAX_TOA_ERR = [0.0]   # largest |GPU - oracle| ToA / widening seen (printed by the last test)
 
 
 @pytest.fixture(scope="module")
@@ -66,7 +73,9 @@ def compare(gpu, ora):
         assert d["w_c"] == pytest.approx(o.w_c, rel=SUM_RTOL * k)
         assert d["q"] == pytest.approx(o.q, rel=SUM_RTOL)
         assert d["p_c"] == pytest.approx(o.p_c, rel=SUM_RTOL * k)
-        assert abs(d["toa"] - o.toa) <= TOA_ATOL * k
+        err = abs(d["toa"] - o.toa)
+        MAX_TOA_ERR[0] = max(MAX_TOA_ERR[0], err / k)
+        assert err <= TOA_ATOL * k, (o.key(), err, k)
 
 
 def demod_bound(x, g1, g0, start, stop):
@@ -341,3 +350,9 @@ def test_exchange_forms_are_bit_identical(torch_cuda, n_chips):
     _, a, na = gpu_run(torch_cuda, w, exchange=1)
     _, b, nb = gpu_run(torch_cuda, w, exchange=2)
     assert na == nb >= 1 and a.tobytes() == b.tobytes()
+
+
+def test_zz_report_toa_error():
+    """Reports the largest ToA difference the comparisons above saw."""
+    print(f"largest FSK ToA difference against the oracle: {MAX_TOA_ERR[0]:.3g} samples (bar {TOA_ATOL})")
+    assert MAX_TOA_ERR[0] <= TOA_ATOL
