@@ -134,6 +134,187 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_corr_dif: the per-code correlation of M = 2^14 points with warp-private
+// second and third passes.
+//
+// The inverse transform is split by decimation in frequency, M = 16 x 1024:
+// with i = j + 1024 m and q = m' + 16 k,
+//   corr[q] = sum_j W_1024^{jk} (W_M^{j m'} sum_m Z[j + 1024 m] W_16^{m m'}),   W = exp(+2 pi i / .)
+// Step A (whole block): thread t loads Z[j + 1024 m] = G * conj(C)/M for the
+// two columns j = t and t + 512, takes their 16-point DFTs over m, multiplies
+// output m' by W_M^{j m'} and stores it at position j of chunk m'.
+// Step B (warp w alone): chunk w is an independent 1024-point inverse DFT,
+// taken as two radix-32 Stockham passes through the chunk's own shared memory
+// (only __syncwarp between them), then |.|^2, the floor sum and the argmax
+// over the lags q = w + 16 k.
+// A block meets only twice per item: before step A writes the chunks (the
+// previous item's chunks are read) and after (the chunks are complete).  In
+// between, warps run out of step: one warp's shared-memory traffic, global
+// loads and arithmetic overlap the others'.  The 16 per-warp partial results
+// are combined by warp 0 after the next item's first barrier.
+// ---------------------------------------------------------------------------
+
+constexpr int kDifChunk = 1024;                          // points per warp transform
+constexpr int kDifChunkPad = kDifChunk + kDifChunk / 32;  // padded chunk pitch (float2)
+constexpr int kDifChunks = 16;                           // M = 2^14 = 16 chunks
+constexpr int kDifThreads = 512;
+
+constexpr size_t dif_smem() {
+  return sizeof(float2) * ((size_t)kDifChunks * kDifChunkPad + TwTables<14>::N + 1024) + 2 * kDifChunks * sizeof(float4);
+}
+
+__device__ __forceinline__ void warp_reduce_stats(float& sum, float& best, int& bt) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, sum, o);
+    const float b2 = __shfl_down_sync(0xffffffffu, best, o);
+    const int t2 = __shfl_down_sync(0xffffffffu, bt, o);
+    sum += s2;
+    better(best, bt, b2, t2);
+  }
+}
+
+template <int LOGM>
+__global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
+  static_assert(LOGM == 14, "16 chunks of 1024 points");
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + kDifChunks * kDifChunkPad;
+  const float2* t32 = sm_tw + TwTables<LOGM>::N;  // W_1024^{a b} at [32 b + a] (forward)
+  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + 1024);  // [2][16]
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int sps = p.sps;
+  load_tables<LOGM>(sm_tw, p.tw);
+  __syncthreads();
+  build_tw32<LOGM>(sm_tw);
+
+
+  const int64_t n_items = p.pairs ? (int64_t)p.n_pairs * sps : (int64_t)sps * p.K * p.nw * p.Cg;
+  int64_t prev_out = -1;
+  int par = 0;
+  for (int64_t item = blockIdx.x;; item += gridDim.x) {
+    const bool have = item < n_items;
+    int64_t out = 0;
+    int rho = 0, qlim = 0;
+    float2 a[16], b[16];
+    if (have) {
+      rho = (int)(item % sps);
+      const int64_t rest = item / sps;
+      int64_t row;
+      int c, w;
+      if (p.pairs) {
+        const int4 pr = p.pairs[rest];
+        row = (int64_t)pr.x * sps + rho;
+        c = pr.y;
+        w = pr.z;
+        out = rest * sps + rho;
+      } else {
+        const int k = (int)(rest % p.K);
+        const int z = (int)(rest / p.K);
+        const int wl = z / p.Cg;
+        c = z % p.Cg;
+        w = p.w0 + wl;
+        row = ((int64_t)wl * p.K + k) * sps + rho;
+        out = (((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho;
+      }
+      const int nvalid = valid_lags(p, w);
+      qlim = (nvalid - rho + sps - 1) / sps;
+      const float2* G = p.G + row * (1 << LOGM);
+      const float2* D = p.D + (int64_t)c * (1 << LOGM);
+      // step A: the two columns' 16-point DFTs and the twiddles of the split
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        a[m] = cmul(G[t + 1024 * m], D[t + 1024 * m]);
+        b[m] = cmul(G[t + 512 + 1024 * m], D[t + 512 + 1024 * m]);
+      }
+      dft_reg<16, +1>(a);
+      dft_reg<16, +1>(b);
+      // output m' times W_M^{j m'}: W_M^{t m'} from the tables every eighth m'
+      // and by repeated multiplication between; W_M^{(t + 512) m'} = W_M^{t m'} W_32^{m'}
+      const float2 wt1 = twiddle<LOGM, +1>(sm_tw, t);
+      float2 wt = wt1;
+#define ATLAS_DIF_TW(M_)                                                                         \
+  if (M_ > 1) wt = ((M_)&7) == 0 ? twiddle<LOGM, +1>(sm_tw, t * (M_)) : cmul(wt, wt1);            \
+  a[M_] = cmul(a[M_], wt);                                                                       \
+  b[M_] = cmul(b[M_], cmul(wt, make_float2(Tw<M_, 32, +1>::re, Tw<M_, 32, +1>::im)));
+      ATLAS_DIF_TW(1) ATLAS_DIF_TW(2) ATLAS_DIF_TW(3) ATLAS_DIF_TW(4) ATLAS_DIF_TW(5) ATLAS_DIF_TW(6)
+      ATLAS_DIF_TW(7) ATLAS_DIF_TW(8) ATLAS_DIF_TW(9) ATLAS_DIF_TW(10) ATLAS_DIF_TW(11) ATLAS_DIF_TW(12)
+      ATLAS_DIF_TW(13) ATLAS_DIF_TW(14) ATLAS_DIF_TW(15)
+#undef ATLAS_DIF_TW
+    }
+    __syncthreads();  // (1) the previous item's chunks are read and its partial results written
+    if (prev_out >= 0 && warp == 0) {
+      float4 r = lane < kDifChunks ? red[(par ^ 1) * kDifChunks + lane]
+                                   : make_float4(0.f, -1.f, __int_as_float(0x7fffffff), 0.f);
+      float sum = r.x, best = r.y;
+      int bt = __float_as_int(r.z);
+      warp_reduce_stats(sum, best, bt);
+      if (lane == 0) p.part[prev_out] = make_float4(sum, best, __int_as_float(bt), 0.f);
+    }
+    if (!have) break;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      sm[m * kDifChunkPad + t + (t >> 5)] = a[m];
+      sm[m * kDifChunkPad + t + 512 + ((t + 512) >> 5)] = b[m];
+    }
+    __syncthreads();  // (2) every chunk is complete
+
+    // step B: warp `warp` transforms chunk `warp` (1024 points) on its own
+    float2* ch = sm + warp * kDifChunkPad;
+    float2 x[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) x[r] = ch[lane + 33 * r];
+    __syncwarp();
+    dft_reg<32, +1>(x);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) ch[33 * lane + r] = x[r];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      x[r] = ch[lane + 33 * r];
+      if (r > 0) {
+        float2 w = t32[32 * r + lane];
+        w.y = -w.y;
+        x[r] = cmul(x[r], w);
+      }
+    }
+    dft_reg<32, +1>(x);
+    // epilogue: lag tau = sps q + rho with q = warp + 16 (lane + 32 r), increasing in r
+    float s0 = 0.f, s1 = 0.f, best = -1.f;
+    int bq = 0x7fffffff;
+    const int q0 = warp + 16 * lane;
+    if (q0 + 16 * 32 * 31 < qlim) {  // every lag of this thread is valid
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const float P = fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
+        if (r & 1) s1 += P; else s0 += P;
+        if (P > best) {
+          best = P;
+          bq = q0 + 512 * r;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const float P = fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
+        if (r & 1) s1 += P; else s0 += P;
+        if (q0 + 512 * r < qlim && P > best) {
+          best = P;
+          bq = q0 + 512 * r;
+        }
+      }
+    }
+    float sum = s0 + s1;
+    int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
+    warp_reduce_stats(sum, best, bt);
+    if (lane == 0) red[par * kDifChunks + warp] = make_float4(sum, best, __int_as_float(bt), 0.f);
+    prev_out = out;
+    par ^= 1;
+  }
+}
+
 template <int LOGH, int LOGE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(fft_threads<LOGH, LOGE>())
     k_window_fft_split(WindowFftParams p) {
@@ -234,6 +415,10 @@ struct FftLaunch {
 
   static cudaError_t prepare() {
     cudaError_t e;
+    void (*dif)(CorrParams) = k_corr_dif<14>;
+    if (LOGE == 5 &&
+        (e = cudaFuncSetAttribute(dif, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dif_smem())) != cudaSuccess)
+      return e;
     if ((e = prepare_one<10>()) != cudaSuccess) return e;
     if ((e = prepare_one<11>()) != cudaSuccess) return e;
     if ((e = prepare_one<12>()) != cudaSuccess) return e;
@@ -303,6 +488,7 @@ struct FftLaunch {
       }
       return cudaGetLastError();
     }
+    if (LOGE == 5 && logM == 14) return corr_dif(p, s);
     switch (logM) {
       case 10: return corr_persistent<10>(p, s);
       case 11: return corr_persistent<11>(p, s);
@@ -311,6 +497,20 @@ struct FftLaunch {
       case 14: return corr_persistent<14>(p, s);
       default: return cudaErrorInvalidValue;
     }
+  }
+
+  // k_corr_dif with as many blocks as fit on the device at once (at most one per cell)
+  static cudaError_t corr_dif(const CorrParams& p, cudaStream_t s) {
+    static int resident = 0;
+    if (resident == 0) {
+      void (*kern)(CorrParams) = k_corr_dif<14>;
+      const cudaError_t e = resident_blocks(kern, kDifThreads, dif_smem(), &resident);
+      if (e != cudaSuccess) return e;
+    }
+    const int64_t items = p.pairs ? (int64_t)p.n_pairs * p.sps : (int64_t)p.sps * p.K * p.nw * p.Cg;
+    const unsigned blocks = (unsigned)std::min<int64_t>(items, resident);
+    k_corr_dif<14><<<blocks, kDifThreads, dif_smem(), s>>>(p);
+    return cudaGetLastError();
   }
 
   // k_corr with as many blocks as fit on the device at once (at most one per cell)
