@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libatlas_acq.so")
 SOURCES = ["acq_kernels.cu", "acq_fft_e4.cu", "acq_fft_e5.cu", "atlas_acq_host.cu", "acq_static.cu", "prop_kernels.cu",
-           "acq_tc.cu", "fsk_kernels.cu", "fsk_fft.cu", "atlas_fsk_host.cu", "atlas_rt_host.cu",
+           "acq_tc5.cu", "fsk_kernels.cu", "fsk_fft.cu", "atlas_fsk_host.cu", "atlas_rt_host.cu",
            "unfused_cufft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

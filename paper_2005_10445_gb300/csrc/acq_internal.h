@@ -122,8 +122,9 @@ cudaError_t launch_pair_stats(const PairStatsParams& p, cudaStream_t s);
 cudaError_t launch_refine(const RefineParams& p, int grid, cudaStream_t s);
 cudaError_t prepare_kernels();  // raises the dynamic shared-memory limits once per process
 // per-code correlation with the inverse transform on the tensor cores
-// (precision 1: FP16 operands, 2: BF16; FP32 accumulation), M = 2^14 only
-cudaError_t launch_corr_tc(int precision, const CorrParams& p, cudaStream_t s);
-cudaError_t prepare_tc();
+// (precision 1: FP16 operands, 2: BF16; FP32 accumulation), M = 2^14 only:
+// tcgen05.mma with TMEM accumulators (acq_tc5.cu)
+cudaError_t launch_corr_tc5(int precision, const CorrParams& p, cudaStream_t s);
+cudaError_t prepare_tc5();
 
 }  // namespace atlas

@@ -470,7 +470,7 @@ cudaError_t prepare_kernels() {
                                 (int)fft_smem<14>())) != cudaSuccess)
     return e;
   if ((e = prepare_fft_e4()) != cudaSuccess) return e;
-  if ((e = prepare_tc()) != cudaSuccess) return e;
+  if ((e = prepare_tc5()) != cudaSuccess) return e;
   return prepare_fft_e5();
 }
 

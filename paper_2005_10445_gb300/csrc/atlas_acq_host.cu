@@ -395,7 +395,7 @@ int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const floa
   const bool timed = profiling && 2 * ctx->ev_used + 1 < (int)ctx->ev.size();
   if (timed) CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used], st));
   if (sel_pending) CK(cudaStreamWaitEvent(st, ctx->ev_sel, 0));  // previous selection has read the partials
-  if (ctx->precision != 0 && g.logM == 14 && !g.split) CK(atlas::launch_corr_tc(ctx->precision, b, st));
+  if (ctx->precision != 0 && g.logM == 14 && !g.split) CK(atlas::launch_corr_tc5(ctx->precision, b, st));
   else CK(atlas::launch_corr(g.logM, g.loge, g.split, b, st));
   if (timed) {
     CK(cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], st));
