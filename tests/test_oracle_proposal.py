@@ -88,3 +88,73 @@ def test_features_ignore_the_overall_level():
     b = pr.features(x * 10.0)
     # log10(P + 1) with P >> 1: scaling by 10 adds 2 to every bin, removed by the mean
     np.testing.assert_allclose(a, b, atol=1e-6)
+
+
+# --- carrier-line features --------------------------------------------------
+
+def _bpsk_window(N=4096, sps=4, fs=1e6, f=1000.0, A=2.5, phase=0.7, seed=4):
+    rng = np.random.default_rng(seed)
+    chips = rng.choice([-1.0, 1.0], size=N // sps)
+    m = np.arange(N)
+    return A * np.repeat(chips, sps) * np.exp(1j * (2 * np.pi * f * m / fs + phase))
+
+
+def test_line_feature_of_a_bpsk_tag_is_closed_form():
+    """A noise-free +/-1-chip tag filling the window at offset f: x^2 is the
+    tone A^2 e^{i(2 pi 2f m/fs + 2 phi)}, so the squared window's DFT at 2 f_j
+    is A^2 times a geometric sum: the ratio to sum |x|^4 = N A^4 is N on the
+    tag's bin and sin^2(pi D N) / (N sin^2(pi D)) elsewhere, D = 2 (f - f_j)/fs."""
+    N, fs, f = 4096, 1e6, 1000.0
+    grid = np.array([-3000.0, -1000.0, 0.0, 1000.0, 1500.0, 3000.0])
+    x = _bpsk_window(N=N, fs=fs, f=f)
+    L = pr.line_features(x, fs, grid)
+    want = []
+    for fj in grid:
+        D = 2.0 * (f - fj) / fs
+        r = float(N) if D == 0 else np.sin(np.pi * D * N) ** 2 / (N * np.sin(np.pi * D) ** 2)
+        want.append(np.log10(r + 1.0))
+    np.testing.assert_allclose(L, want, rtol=1e-9, atol=1e-9)
+    assert int(np.argmax(L)) == 3
+
+
+def test_line_feature_of_noise_is_near_zero_ratio_one():
+    """Complex white noise: E|sum x^2 e|^2 = sum E|x|^4, so the ratio is about 1
+    (log10(2) = 0.3) on every bin, and the feature ignores the overall level."""
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(1 << 15) + 1j * rng.standard_normal(1 << 15)
+    grid = np.linspace(-15500.0, 15500.0, 63)
+    L = pr.line_features(x, 8e6, grid)
+    assert 0.0 < np.mean(L) < 0.6 and np.max(L) < 1.6
+    np.testing.assert_allclose(pr.line_features(1e3 * x, 8e6, grid), L, rtol=1e-9, atol=1e-12)
+
+
+def test_gradients_with_line_features_match_finite_differences():
+    p, f, code, bin_, present = _random_case()
+    p["wl"] = np.array([0.7, -0.4])
+    rng = np.random.default_rng(5)
+    L = rng.uniform(0.0, 3.0, size=(f.shape[0], p["wb"].shape[1]))
+    g = pr.grads(p, f, code, bin_, present, L)
+    for k in ("wl", "wb", "bb", "wp", "bp"):
+        flat = p[k].ravel()
+        for i in range(min(4, flat.size)):
+            old = flat[i]
+            h = 1e-6 * max(1.0, abs(old))
+            flat[i] = old + h
+            lp = pr.loss(p, f, code, bin_, present, L)
+            flat[i] = old - h
+            lm = pr.loss(p, f, code, bin_, present, L)
+            flat[i] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[k].ravel()[i]) <= 1e-6 * max(1.0, abs(fd)), (k, i, fd, g[k].ravel()[i])
+
+
+def test_planted_line_at_f_instead_of_2f_is_caught(monkeypatch):
+    def at_f(xw, fs_hz, freqs_hz):
+        xw = np.asarray(xw, np.complex128)
+        m = np.arange(xw.shape[0], dtype=np.float64)
+        e4 = float(np.sum(np.abs(xw) ** 4))
+        return np.array([np.log10(abs(np.dot(xw * xw, np.exp(-2j * np.pi * (f / fs_hz) * m))) ** 2 / e4 + 1.0)
+                         for f in freqs_hz])
+    monkeypatch.setattr(pr, "line_features", at_f)
+    with pytest.raises(AssertionError):
+        test_line_feature_of_a_bpsk_tag_is_closed_form()
