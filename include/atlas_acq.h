@@ -213,15 +213,22 @@ void atlas_acq_batch_destroy(atlas_acq_batch_t batch);
  * ranks (code, bin) candidates; only the top-k are correlated, and windows
  * where it is not confident fall back to the exhaustive search, which also
  * labels the training data.
- * Network: conv1d (8 channels, kernel 16, stride 8) + ReLU, dense 4096 -> 48
- * + ReLU, heads: code logits [n_codes], bin logits [n_bins], presence logit.
+ * Features per window: one row of 4096 + n_bins floats -- the Welch spectrum,
+ * then n_bins carrier-line values: for +/-1 chips the squared transmission is a
+ * pure tone at twice the carrier offset, so L[k] = log10(|DFT of x^2 at 2 f_k|^2
+ * / sum |x|^4 + 1) shows the bin of a tag (about 0.3 for noise).
+ * Network: conv1d (8 channels, kernel 16, stride 8) + ReLU on the spectrum,
+ * dense 4096 -> 48 + ReLU, heads: code logits [n_codes], bin logits [n_bins]
+ * (+ a L[k]), presence logit (+ c max_k L[k]).
  * Parameters: one FP32 array in the order conv_w [8][16], conv_b [8],
  * w1 [4096][48], b1 [48], wc [48][n_codes], bc [n_codes], wb [48][n_bins],
- * bb [n_bins], wp [48], bp [1]; inference uses an FP16 copy (FP32 accumulate).
+ * bb [n_bins], wp [48], bp [1], wl [2] = (a, c); inference uses an FP16 copy
+ * (FP32 accumulate).
  * ------------------------------------------------------------------------ */
 typedef struct atlas_prop* atlas_prop_t;
 
-/* Create a network with seeded He-uniform weights (1 <= n_codes, n_bins <= 256). */
+/* Create a network with seeded He-uniform weights, zero biases and the
+ * carrier-line weights (a, c) = (4, 1) (1 <= n_codes, n_bins <= 256). */
 int atlas_prop_create(atlas_prop_t* out, int32_t n_codes, int32_t n_bins, uint64_t seed);
 int64_t atlas_prop_num_params(atlas_prop_t p);
 /* Copy the FP32 parameters out to / in from host memory (set resets Adam). */
@@ -229,7 +236,7 @@ int atlas_prop_get_params(atlas_prop_t p, float* h_params);
 int atlas_prop_set_params(atlas_prop_t p, const float* h_params);
 
 /* Checkpoint: the FP32 parameters, the Adam moments and the step count in one
- * file (little-endian): a 40-byte header -- magic "ATLPROP1", uint32 version 1,
+ * file (little-endian): a 40-byte header -- magic "ATLPROP1", uint32 version 2,
  * int32 n_codes, int32 n_bins, uint32 CRC-32 (IEEE 802.3) of the payload,
  * int64 n_params, int64 step -- then params, m, v as float32 [n_params] each.
  * Load checks the magic, version, shapes, length and CRC and returns
@@ -238,9 +245,16 @@ int atlas_prop_set_params(atlas_prop_t p, const float* h_params);
 int atlas_prop_save(atlas_prop_t p, const char* path);
 int atlas_prop_load(atlas_prop_t p, const char* path);
 
+/* Frequency grid of the carrier-line features: fs_hz and the n_freq (= n_bins)
+ * offsets, read during the call (host).  Until it is set the line features are 0. */
+int atlas_prop_set_grid(atlas_prop_t p, double fs_hz, const double* freq_offsets_hz, int32_t n_freq);
+/* Floats in one window's feature row: 4096 + n_bins. */
+int32_t atlas_prop_feature_len(atlas_prop_t p);
+
 /* Features of n_windows windows of window_len samples (a multiple of 4096) starting at
  * first_sample + w * stride of the device stream d_iq [n_samples][2]; samples outside
- * the stream read as zero.  d_feat: device [n_windows][4096]. */
+ * the stream read as zero; the carrier-line phase is window-relative.
+ * d_feat: device [n_windows][atlas_prop_feature_len(p)]. */
 int atlas_prop_features(atlas_prop_t p, void* stream, const float* d_iq, int64_t n_samples, int64_t first_sample,
                         int64_t stride, int32_t window_len, int32_t n_windows, float* d_feat);
 
@@ -265,6 +279,12 @@ int atlas_prop_logits(atlas_prop_t p, void* stream, const float* d_feat, int32_t
 int atlas_prop_candidates(atlas_prop_t p, void* stream, const float* d_feat, int32_t n_windows, int32_t topk,
                           int32_t* d_cand, float* d_conf);
 
+/* Top n_top bins per window by the bin head (ties to the smaller bin), FP16
+ * weights: d_bins [n_windows][n_top] int32; d_conf [n_windows][2] = {probability
+ * mass of the chosen bins, presence probability}.  1 <= n_top <= min(32, n_bins). */
+int atlas_prop_bin_candidates(atlas_prop_t p, void* stream, const float* d_feat, int32_t n_windows, int32_t n_top,
+                              int32_t* d_bins, float* d_conf);
+
 /*
  * Search with the proposal: features and candidates for every window of the
  * context's single code length; each window where the network is confident --
@@ -280,6 +300,19 @@ int atlas_prop_candidates(atlas_prop_t p, void* stream, const float* d_feat, int
 int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, const float* d_iq,
                            int64_t n_samples, int32_t topk, float tau_fb, atlas_detection* d_out, int32_t capacity,
                            int32_t* d_count, int32_t* h_n_fallback);
+
+/*
+ * The same search with bin proposals: a confident window -- probability mass of
+ * its top n_top bins >= tau_fb -- is searched over every code in its top n_top
+ * bins only (n_top of the context's bins, 1 <= n_top <= 32); every other window
+ * by the exhaustive search.  The presence head does not skip windows here: a
+ * weak tag and an empty window have the same features.  The proposal's
+ * carrier-line grid is set from the context.  Otherwise as
+ * atlas_acq_run_proposed.
+ */
+int atlas_acq_run_proposed_bins(atlas_acq_t ctx, atlas_prop_t prop, void* stream, const float* d_iq,
+                                int64_t n_samples, int32_t n_top, float tau_fb, atlas_detection* d_out,
+                                int32_t capacity, int32_t* d_count, int32_t* h_n_fallback);
 
 const char* atlas_prop_last_error(atlas_prop_t p);
 void atlas_prop_destroy(atlas_prop_t p);

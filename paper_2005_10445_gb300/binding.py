@@ -36,6 +36,7 @@ EXPORTED = [
     "atlas_prop_save", "atlas_prop_load",
     "atlas_prop_features", "atlas_prop_loss_grad", "atlas_prop_adam", "atlas_prop_logits", "atlas_prop_candidates",
     "atlas_acq_run_proposed", "atlas_prop_last_error", "atlas_prop_destroy",
+    "atlas_prop_set_grid", "atlas_prop_feature_len", "atlas_prop_bin_candidates", "atlas_acq_run_proposed_bins",
 ]
 # Every symbol include/atlas_unfused.h declares (the comparison pipeline).
 EXPORTED_UNFUSED = ["atlas_unfused_create", "atlas_unfused_run", "atlas_unfused_last_error", "atlas_unfused_destroy"]
@@ -204,6 +205,14 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.atlas_prop_candidates.restype = ctypes.c_int
     lib.atlas_acq_run_proposed.argtypes = [vp, vp, vp, vp, i64, i32, f32, vp, i32, vp, ctypes.POINTER(i32)]
     lib.atlas_acq_run_proposed.restype = ctypes.c_int
+    lib.atlas_acq_run_proposed_bins.argtypes = [vp, vp, vp, vp, i64, i32, f32, vp, i32, vp, ctypes.POINTER(i32)]
+    lib.atlas_acq_run_proposed_bins.restype = ctypes.c_int
+    lib.atlas_prop_set_grid.argtypes = [vp, f64, vp, i32]
+    lib.atlas_prop_set_grid.restype = ctypes.c_int
+    lib.atlas_prop_feature_len.argtypes = [vp]
+    lib.atlas_prop_feature_len.restype = i32
+    lib.atlas_prop_bin_candidates.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    lib.atlas_prop_bin_candidates.restype = ctypes.c_int
     lib.atlas_prop_last_error.argtypes = [vp]
     lib.atlas_prop_last_error.restype = ctypes.c_char_p
     lib.atlas_prop_destroy.argtypes = [vp]
@@ -468,6 +477,7 @@ class Proposal:
         _check(lib.atlas_prop_create(ctypes.byref(self.p), n_codes, n_bins, seed))
         self.n_codes, self.n_bins = n_codes, n_bins
         self.n_params = int(lib.atlas_prop_num_params(self.p))
+        self.feature_len = int(lib.atlas_prop_feature_len(self.p))
 
     def _chk(self, st):
         if st != ATLAS_OK:
@@ -492,6 +502,10 @@ class Proposal:
     def load(self, path: str) -> None:
         self._chk(self._lib.atlas_prop_load(self.p, path.encode()))
 
+    def set_grid(self, fs_hz: float, freqs_hz) -> None:
+        f = np.ascontiguousarray(freqs_hz, np.float64)
+        self._chk(self._lib.atlas_prop_set_grid(self.p, float(fs_hz), f.ctypes.data, f.size))
+
     def features(self, stream: int, d_iq: int, n_samples: int, first: int, stride: int, window_len: int,
                  n_windows: int, d_feat: int) -> None:
         self._chk(self._lib.atlas_prop_features(self.p, stream, d_iq, n_samples, first, stride, window_len,
@@ -512,6 +526,9 @@ class Proposal:
     def candidates(self, stream: int, d_feat: int, n_windows: int, topk: int, d_cand: int, d_conf: int) -> None:
         self._chk(self._lib.atlas_prop_candidates(self.p, stream, d_feat, n_windows, topk, d_cand, d_conf))
 
+    def bin_candidates(self, stream: int, d_feat: int, n_windows: int, n_top: int, d_bins: int, d_conf: int) -> None:
+        self._chk(self._lib.atlas_prop_bin_candidates(self.p, stream, d_feat, n_windows, n_top, d_bins, d_conf))
+
     def close(self) -> None:
         if self.p:
             self._lib.atlas_prop_destroy(self.p)
@@ -530,6 +547,16 @@ def run_proposed(search: "Search", prop: Proposal, stream: int, d_iq: int, n_sam
     nfb = ctypes.c_int32(0)
     _check(load().atlas_acq_run_proposed(search.ctx, prop.p, stream, d_iq, n_samples, topk, float(tau_fb), d_out,
                                          capacity, d_count, ctypes.byref(nfb)), search.ctx)
+    return nfb.value
+
+
+def run_proposed_bins(search: "Search", prop: Proposal, stream: int, d_iq: int, n_samples: int, n_top: int,
+                      tau_fb: float, d_out: int, capacity: int, d_count: int) -> int:
+    """atlas_acq_run_proposed_bins (every code in the top n_top bins of a confident
+    window); returns the number of windows that fell back to the exhaustive search."""
+    nfb = ctypes.c_int32(0)
+    _check(load().atlas_acq_run_proposed_bins(search.ctx, prop.p, stream, d_iq, n_samples, n_top, float(tau_fb),
+                                              d_out, capacity, d_count, ctypes.byref(nfb)), search.ctx)
     return nfb.value
 
 

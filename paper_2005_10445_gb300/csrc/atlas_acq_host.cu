@@ -760,19 +760,26 @@ int atlas_acq_profile_end(atlas_acq_t ctx, atlas_acq_profile* out) {
   return ATLAS_OK;
 }
 
-int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, const float* d_iq,
-                           int64_t n_samples, int32_t topk, float tau_fb, atlas_detection* d_out, int32_t capacity,
-                           int32_t* d_count, int32_t* h_n_fallback) {
+}  // extern "C"
+
+namespace {
+
+// The proposal search: n_sel (code, bin) pairs per window (bins_mode false) or
+// every code in n_sel bins per window (bins_mode true).
+int run_proposed_impl(atlas_acq_t ctx, atlas_prop_t prop, void* stream, const float* d_iq, int64_t n_samples,
+                      int32_t n_sel, bool bins_mode, float tau_fb, atlas_detection* d_out, int32_t capacity,
+                      int32_t* d_count, int32_t* h_n_fallback) {
   const int a = check_run_args(ctx, d_iq, n_samples, d_out, capacity, d_count);
   if (a != ATLAS_OK) return a;
-  if (!prop || topk < 1 || topk > 32 || !(tau_fb >= 0.f)) return ATLAS_ERR_INVALID_ARG;
-  if (prop->lay.C != ctx->C || prop->lay.K != ctx->K) return ATLAS_ERR_INVALID_ARG;
+  if (!prop || n_sel < 1 || n_sel > 32 || !(tau_fb >= 0.f)) return ATLAS_ERR_INVALID_ARG;
+  if (prop->lay.C != ctx->C || prop->lay.K != ctx->K || (bins_mode && n_sel > ctx->K)) return ATLAS_ERR_INVALID_ARG;
   if (ctx->groups.size() != 1 || ctx->groups[0].logM > 14 || ctx->groups[0].N % 4096) return ATLAS_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   const Group& g = ctx->groups[0];
   const int W = g.windows(n_samples);
   const int K = ctx->K, C = ctx->C, sps = ctx->sps;
   const float2* x = reinterpret_cast<const float2*>(d_iq);
+  const int per_window = bins_mode ? n_sel * C : n_sel;  // listed cells per window at most
   // workspaces
   if (prop->ws_windows < W) {
     cudaFree(prop->feat);
@@ -782,13 +789,13 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
     prop->cand = nullptr;
     prop->conf = nullptr;
     prop->ws_windows = 0;
-    if (cudaMalloc((void**)&prop->feat, (size_t)W * 4096 * 4) != cudaSuccess ||
+    if (cudaMalloc((void**)&prop->feat, (size_t)W * atlas_prop_feature_len(prop) * 4) != cudaSuccess ||
         cudaMalloc((void**)&prop->cand, (size_t)W * 32 * 2 * 4) != cudaSuccess ||
         cudaMalloc((void**)&prop->conf, (size_t)W * 2 * 4) != cudaSuccess)
       return ATLAS_ERR_NO_MEMORY;
     prop->ws_windows = W;
   }
-  if (ctx->list_cap < W * topk) {
+  if (ctx->list_cap < W * per_window) {
     cudaFree(ctx->d_items);
     cudaFree(ctx->d_pairs);
     cudaFree(ctx->d_pair_stats);
@@ -796,19 +803,23 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
     ctx->d_pairs = nullptr;
     ctx->d_pair_stats = nullptr;
     ctx->list_cap = 0;
-    if (cudaMalloc((void**)&ctx->d_items, sizeof(int2) * (size_t)W * topk) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->d_pairs, sizeof(int4) * (size_t)W * topk) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->d_pair_stats, sizeof(float4) * (size_t)W * topk) != cudaSuccess)
+    if (cudaMalloc((void**)&ctx->d_items, sizeof(int2) * (size_t)W * per_window) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_pairs, sizeof(int4) * (size_t)W * per_window) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_pair_stats, sizeof(float4) * (size_t)W * per_window) != cudaSuccess)
       return ATLAS_ERR_NO_MEMORY;
-    ctx->list_cap = W * topk;
+    ctx->list_cap = W * per_window;
   }
   if (!ctx->d_fb_count && cudaMalloc((void**)&ctx->d_fb_count, sizeof(int)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
-  // 1-2: features and candidates
-  int r = atlas_prop_features(prop, st, d_iq, n_samples, 0, g.hop, g.N, W, prop->feat);
+  // 1-2: features (spectrum and carrier lines of the context's grid) and candidates
+  int r = atlas_prop_set_grid(prop, ctx->fs, ctx->freqs.data(), K);
   if (r != ATLAS_OK) return r;
-  r = atlas_prop_candidates(prop, st, prop->feat, W, topk, prop->cand, prop->conf);
+  r = atlas_prop_features(prop, st, d_iq, n_samples, 0, g.hop, g.N, W, prop->feat);
   if (r != ATLAS_OK) return r;
-  std::vector<int> cand((size_t)W * topk * 2);
+  r = bins_mode ? atlas_prop_bin_candidates(prop, st, prop->feat, W, n_sel, prop->cand, prop->conf)
+                : atlas_prop_candidates(prop, st, prop->feat, W, n_sel, prop->cand, prop->conf);
+  if (r != ATLAS_OK) return r;
+  const int topk = n_sel;
+  std::vector<int> cand((size_t)W * topk * (bins_mode ? 1 : 2));
   std::vector<float> conf((size_t)W * 2);
   CK(cudaMemcpyAsync(cand.data(), prop->cand, cand.size() * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(conf.data(), prop->conf, conf.size() * 4, cudaMemcpyDeviceToHost, st));
@@ -820,24 +831,37 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
   std::vector<std::vector<int2>> win_items;   // (window, bin)
   std::vector<std::vector<int4>> win_pairs;   // (local item, code, window, bin)
   for (int w = 0; w < W; ++w) {
-    // confident: sure of a (code, bin) pair, or sure the window holds no transmission
-    if (!(std::max(conf[2 * w], 1.f - conf[2 * w + 1]) >= tau_fb)) {
+    // confident -- pairs: sure of a (code, bin) pair, or sure the window holds no
+    // transmission; bins: the proposed bins hold probability mass >= tau_fb (a
+    // window without a visible carrier line is never skipped: a weak tag and an
+    // empty window look alike to the features)
+    const float c_w = bins_mode ? conf[2 * w] : std::max(conf[2 * w], 1.f - conf[2 * w + 1]);
+    if (!(c_w >= tau_fb)) {
       fallback.push_back(w);
       continue;
     }
     std::vector<int2> it;
     std::vector<int4> pr;
-    for (int i = 0; i < topk; ++i) {
-      const int c = cand[((size_t)w * topk + i) * 2], k = cand[((size_t)w * topk + i) * 2 + 1];
-      if (c < 0 || c >= C || k < 0 || k >= K) return ATLAS_ERR_DEVICE;
-      int item = -1;
-      for (int j = 0; j < (int)it.size(); ++j)
-        if (it[j].y == k) item = j;
-      if (item < 0) {
-        item = (int)it.size();
+    if (bins_mode) {  // every code in each proposed bin
+      for (int i = 0; i < topk; ++i) {
+        const int k = cand[(size_t)w * topk + i];
+        if (k < 0 || k >= K) return ATLAS_ERR_DEVICE;
         it.push_back(make_int2(w, k));
+        for (int c = 0; c < C; ++c) pr.push_back(make_int4(i, c, w, k));
       }
-      pr.push_back(make_int4(item, c, w, k));
+    } else {
+      for (int i = 0; i < topk; ++i) {
+        const int c = cand[((size_t)w * topk + i) * 2], k = cand[((size_t)w * topk + i) * 2 + 1];
+        if (c < 0 || c >= C || k < 0 || k >= K) return ATLAS_ERR_DEVICE;
+        int item = -1;
+        for (int j = 0; j < (int)it.size(); ++j)
+          if (it[j].y == k) item = j;
+        if (item < 0) {
+          item = (int)it.size();
+          it.push_back(make_int2(w, k));
+        }
+        pr.push_back(make_int4(item, c, w, k));
+      }
     }
     win.push_back(w);
     win_items.push_back(it);
@@ -996,6 +1020,24 @@ int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, con
   CK(cudaStreamSynchronize(st));
   if (h_n_fallback) *h_n_fallback = (int)fallback.size();
   return ATLAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int atlas_acq_run_proposed(atlas_acq_t ctx, atlas_prop_t prop, void* stream, const float* d_iq,
+                           int64_t n_samples, int32_t topk, float tau_fb, atlas_detection* d_out, int32_t capacity,
+                           int32_t* d_count, int32_t* h_n_fallback) {
+  return run_proposed_impl(ctx, prop, stream, d_iq, n_samples, topk, false, tau_fb, d_out, capacity, d_count,
+                           h_n_fallback);
+}
+
+int atlas_acq_run_proposed_bins(atlas_acq_t ctx, atlas_prop_t prop, void* stream, const float* d_iq,
+                                int64_t n_samples, int32_t n_top, float tau_fb, atlas_detection* d_out,
+                                int32_t capacity, int32_t* d_count, int32_t* h_n_fallback) {
+  return run_proposed_impl(ctx, prop, stream, d_iq, n_samples, n_top, true, tau_fb, d_out, capacity, d_count,
+                           h_n_fallback);
 }
 
 int atlas_acq_last_device_status(atlas_acq_t ctx) {

@@ -7,14 +7,18 @@
 // network ranks (code, bin) candidates from a window's power spectrum, the
 // exhaustive search produces its training labels and stays as the fallback.
 //
-// Network: features f[4096] -> conv1d (8 channels, kernel 16, stride 8) + ReLU
-// -> dense 4096 -> 48 + ReLU -> heads: code logits [C], bin logits [K],
-// presence logit.  Loss per window: BCE(presence) + present * (CE(code) +
-// CE(bin)), averaged over the batch.  Parameters are one FP32 array in the
-// order conv_w [8][16], conv_b [8], w1 [4096][48], b1 [48], wc [48][C], bc [C],
-// wb [48][K], bb [K], wp [48], bp [1]; inference can run on an FP16 copy of the
-// weights (FP32 accumulation).  Every reduction has a fixed order, so results
-// are bit-reproducible.
+// Features per window (one row of 4096 + K floats): the Welch log power
+// spectrum f[4096], then K carrier-line values L[k] (for +/-1 chips the squared
+// transmission is a pure tone at twice the carrier offset; L[k] = log10 of the
+// squared window's |DFT|^2 at 2 f_k over sum |x|^4, plus 1).
+// Network: f -> conv1d (8 channels, kernel 16, stride 8) + ReLU -> dense 4096
+// -> 48 + ReLU -> heads: code logits [C], bin logits [K] (+ a L[k]), presence
+// logit (+ c max_k L[k]).  Loss per window: BCE(presence) + present *
+// (CE(code) + CE(bin)), averaged over the batch.  Parameters are one FP32
+// array in the order conv_w [8][16], conv_b [8], w1 [4096][48], b1 [48],
+// wc [48][C], bc [C], wb [48][K], bb [K], wp [48], bp [1], wl [2] = (a, c);
+// inference can run on an FP16 copy of the weights (FP32 accumulation).
+// Every reduction has a fixed order, so results are bit-reproducible.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -28,6 +32,7 @@
 
 #include "acq_common.cuh"
 #include "atlas_acq.h"
+#include "host_util.h"
 #include "prop_internal.h"
 
 namespace atlas {
@@ -54,9 +59,12 @@ Layout make_layout(int C, int K) {
   l.bb = o; o += K;
   l.wp = o; o += kHid;
   l.bp = o; o += 1;
+  l.wl = o; o += 2;
   l.total = o;
   return l;
 }
+
+int feature_len(int K) { return kSeg + K; }
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
@@ -68,7 +76,7 @@ __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 constexpr int kPsdThreads = kSeg / 32;  // 128 threads x 32 values
 
 __global__ void __launch_bounds__(kPsdThreads) k_psd(const float2* x, int64_t S, int64_t first, int64_t stride,
-                                                      int n_seg, const float2* tw, float* feat) {
+                                                      int n_seg, const float2* tw, float* feat, int row_len) {
   using FFT = BlockFFT<12, 5, -1>;
   __shared__ float2 sm[FFT::SMEM_ELEMS];
   __shared__ float2 sm_tw[TwTables<12>::N];
@@ -111,9 +119,137 @@ __global__ void __launch_bounds__(kPsdThreads) k_psd(const float2* x, int64_t S,
   float tot = 0.f;
   for (int i = 0; i < kPsdThreads / 32; ++i) tot += red[i];
   const float mean = tot * (1.0f / kSeg);
-  float* out = feat + (int64_t)blockIdx.x * kSeg;
+  float* out = feat + (int64_t)blockIdx.x * row_len;
 #pragma unroll
   for (int i = 0; i < 32; ++i) out[t + kPsdThreads * i] = acc[i] - mean;
+}
+
+// ---------------------------------------------------------------------------
+// carrier-line features: L[k] = log10(|sum_m x[m]^2 e^{-2 pi i 2 f_k m / fs}|^2
+// / sum_m |x[m]|^4 + 1) over one window (m window-relative).  One block per
+// window; the window goes through shared memory in chunks of kLineChunk
+// samples (squared on the way in); thread (r, k) accumulates bin k over the
+// r-th eighth of each chunk with a phasor that starts exactly (64-bit
+// fixed-point phase of 2 f_k) and advances by one complex product per sample.
+// ---------------------------------------------------------------------------
+
+constexpr int kLineThreads = 512;
+constexpr int kLineChunk = 4096;
+constexpr int kLineSub = 8;                      // sub-ranges per chunk
+constexpr int kLineBinsPerPass = kLineThreads / kLineSub;  // 64
+
+__global__ void __launch_bounds__(kLineThreads) k_line(const float2* x, int64_t S, int64_t first, int64_t stride,
+                                                       int N, const uint64_t* inc2, int K, float* feat,
+                                                       int row_len) {
+  __shared__ float2 x2[kLineChunk];
+  __shared__ float2 part[kLineSub][kLineBinsPerPass];
+  __shared__ float red[kLineThreads / 32];
+  const int t = threadIdx.x, r = t / kLineBinsPerPass, kk = t % kLineBinsPerPass;
+  const int64_t base = first + (int64_t)blockIdx.x * stride;
+  constexpr int kPasses = 4;  // up to 256 bins
+  float2 acc[kPasses];
+#pragma unroll
+  for (int g = 0; g < kPasses; ++g) acc[g] = make_float2(0.f, 0.f);
+  float e4 = 0.f;
+  for (int c0 = 0; c0 < N; c0 += kLineChunk) {
+    __syncthreads();  // the previous chunk is consumed
+    for (int i = t; i < kLineChunk; i += kLineThreads) {
+      const int64_t idx = base + c0 + i;
+      const float2 v = (c0 + i < N && idx >= 0 && idx < S) ? x[idx] : make_float2(0.f, 0.f);
+      const float2 v2 = make_float2(fmaf(v.x, v.x, -v.y * v.y), 2.f * v.x * v.y);
+      x2[i] = v2;
+      e4 = fmaf(v2.x, v2.x, fmaf(v2.y, v2.y, e4));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < kPasses; ++g) {
+      const int k = kk + g * kLineBinsPerPass;
+      if (k >= K) break;
+      const int m0 = c0 + r * (kLineChunk / kLineSub);
+      float2 ph = expi_neg(inc2[k] * (uint64_t)m0);
+      const float2 step = expi_neg(inc2[k]);
+      float2 a = acc[g];
+      const float2* src = x2 + r * (kLineChunk / kLineSub);
+      for (int i = 0; i < kLineChunk / kLineSub; ++i) {
+        const float2 v = src[i];
+        a.x = fmaf(v.x, ph.x, fmaf(-v.y, ph.y, a.x));
+        a.y = fmaf(v.x, ph.y, fmaf(v.y, ph.x, a.y));
+        ph = cmul(ph, step);
+      }
+      acc[g] = a;
+    }
+  }
+  // total |x|^4 (fixed order)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e4 += __shfl_down_sync(0xffffffffu, e4, o);
+  if ((t & 31) == 0) red[t >> 5] = e4;
+  __syncthreads();
+  float tot = 0.f;
+  for (int i = 0; i < kLineThreads / 32; ++i) tot += red[i];
+  float* out = feat + (int64_t)blockIdx.x * row_len + kSeg;
+  for (int g = 0; g < kPasses; ++g) {
+    if (g * kLineBinsPerPass >= K) break;
+    __syncthreads();
+    part[r][kk] = acc[g];
+    __syncthreads();
+    const int k = kk + g * kLineBinsPerPass;
+    if (r == 0 && k < K) {
+      float2 s2 = part[0][kk];
+      for (int q = 1; q < kLineSub; ++q) s2 = make_float2(s2.x + part[q][kk].x, s2.y + part[q][kk].y);
+      const float p2 = fmaf(s2.x, s2.x, s2.y * s2.y);
+      out[k] = tot > 0.f ? log10f(p2 / tot + 1.f) : 0.f;
+    }
+  }
+}
+
+// bin logit k += a L[k]; presence logit += c max_k L[k]  (one thread per window)
+template <typename TW>
+__global__ void k_line_heads(const float* f, int row_len, int K, const TW* wl, int B, float* zb, float* zp) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float a = to_f(wl[0]), c = to_f(wl[1]);
+  const float* L = f + (int64_t)b * row_len + kSeg;
+  float mx = -INFINITY;
+  for (int k = 0; k < K; ++k) {
+    zb[(int64_t)b * K + k] = fmaf(a, L[k], zb[(int64_t)b * K + k]);
+    mx = fmaxf(mx, L[k]);
+  }
+  zp[b] = fmaf(c, mx, zp[b]);
+}
+
+// g_a = sum_b sum_k dzb[b][k] L[b][k], g_c = sum_b dzp[b] max_k L[b][k]  (one block, fixed order)
+__global__ void __launch_bounds__(256) k_line_grad(const float* f, int row_len, int K, int B, const float* dzb,
+                                                   const float* dzp, float* g) {
+  __shared__ float red[2][8];
+  float ga = 0.f, gc = 0.f;
+  for (int b = threadIdx.x; b < B; b += 256) {
+    const float* L = f + (int64_t)b * row_len + kSeg;
+    float mx = -INFINITY;
+    for (int k = 0; k < K; ++k) {
+      ga = fmaf(dzb[(int64_t)b * K + k], L[k], ga);
+      mx = fmaxf(mx, L[k]);
+    }
+    gc = fmaf(dzp[b], mx, gc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ga += __shfl_down_sync(0xffffffffu, ga, o);
+    gc += __shfl_down_sync(0xffffffffu, gc, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ga;
+    red[1][threadIdx.x >> 5] = gc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, c = 0.f;
+    for (int i = 0; i < 8; ++i) {
+      a += red[0][i];
+      c += red[1][i];
+    }
+    g[0] = a;
+    g[1] = c;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -162,9 +298,10 @@ static void gemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, c
 // ---------------------------------------------------------------------------
 
 template <typename TW>
-__global__ void __launch_bounds__(kP) k_conv_fwd(const float* f, const TW* w, const TW* b, float* a1p, float* x1) {
+__global__ void __launch_bounds__(kP) k_conv_fwd(const float* f, int row_len, const TW* w, const TW* b, float* a1p,
+                                                 float* x1) {
   __shared__ float fs[kSeg + kKw];
-  const float* fb = f + (int64_t)blockIdx.x * kSeg;
+  const float* fb = f + (int64_t)blockIdx.x * row_len;
   for (int i = threadIdx.x; i < kSeg + kKw; i += kP) fs[i] = i < kSeg ? fb[i] : 0.f;
   __syncthreads();
   const int p = threadIdx.x;
@@ -180,7 +317,8 @@ __global__ void __launch_bounds__(kP) k_conv_fwd(const float* f, const TW* w, co
 }
 
 // g[o][t] = sum_b sum_p da1p[b][o][p] f[b][8p + t]  (blocks 0 .. 127), g_b[o] = sum da1p (blocks 128 .. 135)
-__global__ void __launch_bounds__(256) k_conv_bwd(const float* f, const float* da1p, int B, float* gw, float* gb) {
+__global__ void __launch_bounds__(256) k_conv_bwd(const float* f, int row_len, const float* da1p, int B, float* gw,
+                                                  float* gb) {
   __shared__ float red[8];
   const int id = blockIdx.x;
   const bool bias = id >= kCh * kKw;
@@ -194,7 +332,7 @@ __global__ void __launch_bounds__(256) k_conv_bwd(const float* f, const float* d
       acc += d;
     } else {
       const int j = kSt * p + t;
-      acc = fmaf(d, j < kSeg ? f[(int64_t)b * kSeg + j] : 0.f, acc);
+      acc = fmaf(d, j < kSeg ? f[(int64_t)b * row_len + j] : 0.f, acc);
     }
   }
 #pragma unroll
@@ -377,6 +515,44 @@ __global__ void __launch_bounds__(256) k_candidates(const float* zc, const float
   }
 }
 
+// ---------------------------------------------------------------------------
+// bin candidates: the top-nb bins by the bin head (ties to the smaller bin),
+// every code searched in them; conf = {probability mass of the chosen bins,
+// presence probability}
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(32) k_bin_candidates(const float* zb, const float* zp, int K, int nb, int* bins,
+                                                       float* conf) {
+  __shared__ float lb[256];
+  const int w = blockIdx.x, t = threadIdx.x;
+  const float* z = zb + (int64_t)w * K;
+  float mx = -INFINITY;
+  for (int i = t; i < K; i += 32) mx = fmaxf(mx, z[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float se = 0.f;
+  for (int i = t; i < K; i += 32) se += expf(z[i] - mx);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+  const float lse = mx + logf(se);
+  for (int i = t; i < K; i += 32) lb[i] = z[i] - lse;
+  __syncwarp();
+  if (t == 0) {
+    uint64_t taken[4] = {0, 0, 0, 0};
+    float mass = 0.f;
+    for (int r = 0; r < nb; ++r) {
+      int bi = -1;
+      for (int k = 0; k < K; ++k)
+        if (!((taken[k >> 6] >> (k & 63)) & 1) && (bi < 0 || lb[k] > lb[bi])) bi = k;
+      taken[bi >> 6] |= 1ull << (bi & 63);
+      bins[(int64_t)w * nb + r] = bi;
+      mass += expf(lb[bi]);
+    }
+    conf[2 * w + 0] = mass;
+    conf[2 * w + 1] = 1.f / (1.f + expf(-zp[w]));
+  }
+}
+
 }  // namespace prop
 }  // namespace atlas
 
@@ -404,7 +580,7 @@ void free_prop(atlas_prop* p) {
   for (void* ptr : {(void*)p->params, (void*)p->half, (void*)p->grad, (void*)p->m, (void*)p->v, (void*)p->a1p,
                     (void*)p->x1, (void*)p->dx1, (void*)p->hp, (void*)p->h, (void*)p->zc, (void*)p->zb, (void*)p->zp,
                     (void*)p->dzc, (void*)p->dzb, (void*)p->dzp, (void*)p->dh, (void*)p->loss, (void*)p->tw,
-                    (void*)p->feat, (void*)p->cand, (void*)p->conf})
+                    (void*)p->feat, (void*)p->cand, (void*)p->conf, (void*)p->inc2})
     cudaFree(ptr);
   delete p;
 }
@@ -446,23 +622,25 @@ int ensure_batch(atlas_prop* p, int B) {
 // forward pass on batch B; with half weights when `half` (inference) else FP32 (training)
 int forward(atlas_prop* p, cudaStream_t s, const float* f, int B, bool half) {
   const Layout& L = p->lay;
-  const int C = L.C, K = L.K;
+  const int C = L.C, K = L.K, R = feature_len(K);
   if (half) {
     const __half* w = p->half;
-    k_conv_fwd<__half><<<B, kP, 0, s>>>(f, w + L.conv_w, w + L.conv_b, nullptr, p->x1);
+    k_conv_fwd<__half><<<B, kP, 0, s>>>(f, R, w + L.conv_w, w + L.conv_b, nullptr, p->x1);
     gemm<false, false, __half>(s, B, kHid, kX1, p->x1, kX1, w + L.w1, kHid, p->h, kHid, w + L.b1, 1, 0.f);
     gemm<false, false, __half>(s, B, C, kHid, p->h, kHid, w + L.wc, C, p->zc, C, w + L.bc, 0, 0.f);
     gemm<false, false, __half>(s, B, K, kHid, p->h, kHid, w + L.wb, K, p->zb, K, w + L.bb, 0, 0.f);
     gemm<false, false, __half>(s, B, 1, kHid, p->h, kHid, w + L.wp, 1, p->zp, 1, w + L.bp, 0, 0.f);
+    k_line_heads<__half><<<(B + 127) / 128, 128, 0, s>>>(f, R, K, w + L.wl, B, p->zb, p->zp);
   } else {
     const float* w = p->params;
-    k_conv_fwd<float><<<B, kP, 0, s>>>(f, w + L.conv_w, w + L.conv_b, p->a1p, p->x1);
+    k_conv_fwd<float><<<B, kP, 0, s>>>(f, R, w + L.conv_w, w + L.conv_b, p->a1p, p->x1);
     gemm<false, false, float>(s, B, kHid, kX1, p->x1, kX1, w + L.w1, kHid, p->hp, kHid, w + L.b1, 0, 0.f);
     cudaMemcpyAsync(p->h, p->hp, (size_t)B * kHid * 4, cudaMemcpyDeviceToDevice, s);
     k_mask_relu<<<(B * kHid + 255) / 256, 256, 0, s>>>(p->h, p->hp, (int64_t)B * kHid);
     gemm<false, false, float>(s, B, C, kHid, p->h, kHid, w + L.wc, C, p->zc, C, w + L.bc, 0, 0.f);
     gemm<false, false, float>(s, B, K, kHid, p->h, kHid, w + L.wb, K, p->zb, K, w + L.bb, 0, 0.f);
     gemm<false, false, float>(s, B, 1, kHid, p->h, kHid, w + L.wp, 1, p->zp, 1, w + L.bp, 0, 0.f);
+    k_line_heads<float><<<(B + 127) / 128, 128, 0, s>>>(f, R, K, w + L.wl, B, p->zb, p->zp);
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ATLAS_OK : fail(p, e);
@@ -502,6 +680,10 @@ int atlas_prop_create(atlas_prop_t* out, int32_t n_codes, int32_t n_bins, uint64
   fill(L.wc, (size_t)kHid * L.C, kHid);
   fill(L.wb, (size_t)kHid * L.K, kHid);
   fill(L.wp, kHid, kHid);
+  // the carrier-line weights start from a prior: a line raises its bin's logit
+  // (a = 4 per log10 unit) and the presence logit (c = 1); training adjusts both
+  h[L.wl] = 4.f;
+  h[L.wl + 1] = 1.f;
   int st2 = ATLAS_OK;
   cudaError_t e = cudaMemcpy(p->params, h.data(), n * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p->m, 0, n * 4);
@@ -564,7 +746,7 @@ static uint32_t crc32_update(uint32_t crc, const unsigned char* d, size_t n) {
 
 namespace {
 constexpr char kCkptMagic[8] = {'A', 'T', 'L', 'P', 'R', 'O', 'P', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;  // 2: the carrier-line head weights wl follow bp
 struct CkptHeader {  // 40 bytes, little-endian
   char magic[8];
   uint32_t version;
@@ -628,10 +810,31 @@ int atlas_prop_features(atlas_prop_t p, void* stream, const float* d_iq, int64_t
                         int64_t stride, int32_t window_len, int32_t n_windows, float* d_feat) {
   if (!p || !d_iq || !d_feat || n_samples <= 0 || n_windows <= 0 || window_len < kSeg || stride <= 0)
     return ATLAS_ERR_INVALID_ARG;
-  k_psd<<<n_windows, kPsdThreads, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(d_iq), n_samples,
-                                                               first_sample, stride, window_len / kSeg, p->tw,
-                                                               d_feat);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int R = feature_len(p->lay.K);
+  k_psd<<<n_windows, kPsdThreads, 0, s>>>(reinterpret_cast<const float2*>(d_iq), n_samples, first_sample, stride,
+                                          window_len / kSeg, p->tw, d_feat, R);
+  if (p->inc2) {
+    k_line<<<n_windows, kLineThreads, 0, s>>>(reinterpret_cast<const float2*>(d_iq), n_samples, first_sample, stride,
+                                              window_len, p->inc2, p->lay.K, d_feat, R);
+  } else {
+    PCK(cudaMemset2DAsync(d_feat + kSeg, (size_t)R * 4, 0, (size_t)p->lay.K * 4, n_windows, s));
+  }
   PCK(cudaGetLastError());
+  return ATLAS_OK;
+}
+
+int32_t atlas_prop_feature_len(atlas_prop_t p) { return p ? feature_len(p->lay.K) : -1; }
+
+int atlas_prop_set_grid(atlas_prop_t p, double fs_hz, const double* freq_offsets_hz, int32_t n_freq) {
+  if (!p || !freq_offsets_hz || !(fs_hz > 0.0) || n_freq != p->lay.K) return ATLAS_ERR_INVALID_ARG;
+  std::vector<uint64_t> inc2(n_freq);
+  for (int k = 0; k < n_freq; ++k) {
+    if (!isfinite(freq_offsets_hz[k])) return ATLAS_ERR_INVALID_ARG;
+    inc2[k] = 2ull * atlas::phase_increment(freq_offsets_hz[k], fs_hz);  // 2 f_k, modulo one turn
+  }
+  if (!p->inc2) PCK(cudaMalloc((void**)&p->inc2, sizeof(uint64_t) * n_freq));
+  PCK(cudaMemcpy(p->inc2, inc2.data(), sizeof(uint64_t) * n_freq, cudaMemcpyHostToDevice));
   return ATLAS_OK;
 }
 
@@ -649,6 +852,7 @@ int atlas_prop_loss_grad(atlas_prop_t p, void* stream, const float* d_feat, cons
   k_heads_loss<<<(B + 7) / 8, 256, 0, s>>>(p->zc, p->zb, p->zp, d_code, d_bin, B, C, K, p->dzc, p->dzb, p->dzp,
                                            p->loss);
   k_mean<<<1, 256, 0, s>>>(p->loss, B, d_loss);
+  k_line_grad<<<1, 256, 0, s>>>(d_feat, feature_len(K), K, B, p->dzb, p->dzp, g + L.wl);
   // head weight and bias gradients
   gemm<true, false, float>(s, kHid, C, B, p->h, kHid, p->dzc, C, g + L.wc, C, nullptr, 0, 0.f);
   gemm<true, false, float>(s, kHid, K, B, p->h, kHid, p->dzb, K, g + L.wb, K, nullptr, 0, 0.f);
@@ -666,7 +870,7 @@ int atlas_prop_loss_grad(atlas_prop_t p, void* stream, const float* d_feat, cons
   // dx1 = dh w1^T, masked by ReLU of the conv outputs
   gemm<false, true, float>(s, B, kX1, kHid, p->dh, kHid, w + L.w1, kHid, p->dx1, kX1, nullptr, 0, 0.f);
   k_mask_relu<<<(unsigned)(((int64_t)B * kX1 + 255) / 256), 256, 0, s>>>(p->dx1, p->a1p, (int64_t)B * kX1);
-  k_conv_bwd<<<kCh * kKw + kCh, 256, 0, s>>>(d_feat, p->dx1, B, g + L.conv_w, g + L.conv_b);
+  k_conv_bwd<<<kCh * kKw + kCh, 256, 0, s>>>(d_feat, feature_len(K), p->dx1, B, g + L.conv_w, g + L.conv_b);
   PCK(cudaGetLastError());
   return ATLAS_OK;
 }
@@ -709,6 +913,19 @@ int atlas_prop_candidates(atlas_prop_t p, void* stream, const float* d_feat, int
   if (st != ATLAS_OK) return st;
   if ((st = forward(p, s, d_feat, n_windows, true)) != ATLAS_OK) return st;
   k_candidates<<<n_windows, 256, 0, s>>>(p->zc, p->zb, p->zp, p->lay.C, p->lay.K, topk, d_cand, d_conf);
+  PCK(cudaGetLastError());
+  return ATLAS_OK;
+}
+
+int atlas_prop_bin_candidates(atlas_prop_t p, void* stream, const float* d_feat, int32_t n_windows, int32_t n_top,
+                              int32_t* d_bins, float* d_conf) {
+  if (!p || !d_feat || n_windows <= 0 || n_top <= 0 || n_top > 32 || n_top > p->lay.K || !d_bins || !d_conf)
+    return ATLAS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = ensure_batch(p, n_windows);
+  if (st != ATLAS_OK) return st;
+  if ((st = forward(p, s, d_feat, n_windows, true)) != ATLAS_OK) return st;
+  k_bin_candidates<<<n_windows, 32, 0, s>>>(p->zb, p->zp, p->lay.K, n_top, d_bins, d_conf);
   PCK(cudaGetLastError());
   return ATLAS_OK;
 }

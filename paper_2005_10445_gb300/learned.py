@@ -48,7 +48,9 @@ def labels_from(dets, n_windows: int) -> Tuple[np.ndarray, np.ndarray]:
 
 
 def features(prop: binding.Proposal, x, n_samples: int, n_windows: int, hop: int, N: int, torch):
-    feat = torch.empty(n_windows * 4096, dtype=torch.float32, device=x.device)
+    """Feature rows [n_windows][prop.feature_len]: the spectrum, then the
+    carrier-line values of the grid set on `prop` (zeros without one)."""
+    feat = torch.empty(n_windows * prop.feature_len, dtype=torch.float32, device=x.device)
     st = torch.cuda.current_stream(x.device)
     prop.features(st.cuda_stream, x.data_ptr(), n_samples, 0, hop, N, n_windows, feat.data_ptr())
     return feat
@@ -60,7 +62,7 @@ def train(prop: binding.Proposal, feat, code: np.ndarray, bin_: np.ndarray, torc
     n = code.shape[0]
     d_code = torch.from_numpy(code).to(dev)
     d_bin = torch.from_numpy(bin_).to(dev)
-    f2 = feat.view(n, 4096)
+    f2 = feat.view(n, prop.feature_len)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev)
     rng = np.random.default_rng(seed)
@@ -82,17 +84,21 @@ def train(prop: binding.Proposal, feat, code: np.ndarray, bin_: np.ndarray, torc
 
 
 def evaluate(search: binding.Search, prop: binding.Proposal, x, n_samples: int, exh_dets, exh_time: float,
-             topk: int, tau: float, capacity: int, torch) -> Dict[str, float]:
+             topk: int, tau: float, capacity: int, torch, bins: bool = False) -> Dict[str, float]:
+    """Recall, speedup and ToA difference of the proposal search against the
+    exhaustive one.  bins=False: the top-k (code, bin) pairs of a confident
+    window; bins=True: every code in its top-k bins."""
     dev = x.device
     out = torch.zeros(capacity * 32, dtype=torch.uint8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
     st = torch.cuda.current_stream(dev)
-    binding.run_proposed(search, prop, st.cuda_stream, x.data_ptr(), n_samples, topk, tau, out.data_ptr(), capacity,
-                         cnt.data_ptr())  # warm the workspaces
+    run = binding.run_proposed_bins if bins else binding.run_proposed
+    run(search, prop, st.cuda_stream, x.data_ptr(), n_samples, topk, tau, out.data_ptr(), capacity,
+        cnt.data_ptr())  # warm the workspaces
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    nfb = binding.run_proposed(search, prop, st.cuda_stream, x.data_ptr(), n_samples, topk, tau, out.data_ptr(),
-                               capacity, cnt.data_ptr())
+    nfb = run(search, prop, st.cuda_stream, x.data_ptr(), n_samples, topk, tau, out.data_ptr(), capacity,
+              cnt.data_ptr())
     dt = time.perf_counter() - t0
     n = int(cnt.item())
     got = out.cpu().numpy().view(binding.DETECTION_DTYPE)[: min(n, capacity)]
@@ -102,6 +108,7 @@ def evaluate(search: binding.Search, prop: binding.Proposal, x, n_samples: int, 
     hit = len(exh & prp)
     toa = {key(d): float(d["toa"]) for d in exh_dets}
     toa_err = max([abs(float(d["toa"]) - toa[key(d)]) for d in got if key(d) in toa] or [0.0])
-    return {"tau_fb": tau, "topk": topk, "recall": hit / max(len(exh), 1), "exhaustive_detections": len(exh),
+    return {"mode": "bins" if bins else "pairs", "tau_fb": tau, "topk": topk, "recall": hit / max(len(exh), 1),
+            "exhaustive_detections": len(exh),
             "proposal_detections": len(prp), "extra_detections": len(prp - exh), "fallback_windows": nfb,
             "time_s": dt, "speedup": exh_time / dt, "max_toa_diff_samples": toa_err}

@@ -30,25 +30,57 @@ def _net(torch, C, K, seed=0):
     return net, pr.unflatten(pr.flatten(p).astype(np.float32).astype(np.float64), C, K)
 
 
-def test_features_match_oracle(torch_cuda):
-    torch = torch_cuda
-    from paper_2005_10445_gb300.binding import Proposal
-    net = Proposal(4, 3, 0)
-    wl = synth.small(seed=11)
-    x = torch.from_numpy(wl.iq().copy()).cuda()
-    n_win, stride, wlen = 5, 5000, 2 * pr.SEG
-    feat = torch.empty(n_win * pr.SEG, dtype=torch.float32, device="cuda")
-    st = torch.cuda.current_stream()
-    net.features(st.cuda_stream, x.data_ptr(), wl.n_samples, 1234, stride, wlen, n_win, feat.data_ptr())
-    st.synchronize()
-    got = feat.cpu().numpy().reshape(n_win, pr.SEG)
+def _windows(wl, first, stride, wlen, n_win):
     xs = wl.x.astype(np.complex128)
+    out = []
     for w in range(n_win):
-        a = 1234 + w * stride
+        a = first + w * stride
         seg = np.zeros(wlen, np.complex128)
         hi = min(a + wlen, wl.n_samples)
         seg[: hi - a] = xs[a:hi]
-        np.testing.assert_allclose(got[w], pr.features(seg), atol=1e-4)
+        out.append(seg)
+    return out
+
+
+def test_features_match_oracle(torch_cuda):
+    """Spectrum features, and zero carrier-line features while no grid is set."""
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import Proposal
+    net = Proposal(4, 3, 0)
+    assert net.feature_len == pr.SEG + 3
+    wl = synth.small(seed=11)
+    x = torch.from_numpy(wl.iq().copy()).cuda()
+    n_win, stride, wlen = 5, 5000, 2 * pr.SEG
+    feat = torch.empty(n_win * net.feature_len, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    net.features(st.cuda_stream, x.data_ptr(), wl.n_samples, 1234, stride, wlen, n_win, feat.data_ptr())
+    st.synchronize()
+    got = feat.cpu().numpy().reshape(n_win, net.feature_len)
+    for w, seg in enumerate(_windows(wl, 1234, stride, wlen, n_win)):
+        np.testing.assert_allclose(got[w, :pr.SEG], pr.features(seg), atol=1e-4)
+    assert (got[:, pr.SEG:] == 0).all()
+
+
+def test_line_features_match_oracle(torch_cuda):
+    """Carrier-line features on the GPU (FP32, exact fixed-point phase, phasor
+    steps within a chunk) against the FP64 definition, on windows with tags,
+    noise only and the zero-padded stream end; bounded in log10 units."""
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import Proposal
+    wl = synth.small(seed=12, snr_range=(0.0, 6.0))
+    K = len(wl.freqs_hz)
+    net = Proposal(len(wl.chips), K, 0)
+    net.set_grid(wl.fs_hz, wl.freqs_hz)
+    x = torch.from_numpy(wl.iq().copy()).cuda()
+    n_win, stride, wlen = 9, 4500, 2 * pr.SEG
+    feat = torch.empty(n_win * net.feature_len, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    net.features(st.cuda_stream, x.data_ptr(), wl.n_samples, 0, stride, wlen, n_win, feat.data_ptr())
+    st.synchronize()
+    got = feat.cpu().numpy().reshape(n_win, net.feature_len)[:, pr.SEG:]
+    want = np.array([pr.line_features(seg, wl.fs_hz, wl.freqs_hz) for seg in _windows(wl, 0, stride, wlen, n_win)])
+    np.testing.assert_allclose(got, want, atol=2e-3)
+    assert want.max() > 1.5  # some window holds a strong line
 
 
 def test_logits_and_gradients_match_oracle(torch_cuda):
@@ -57,12 +89,13 @@ def test_logits_and_gradients_match_oracle(torch_cuda):
     net, p = _net(torch, C, K, seed=3)
     rng = np.random.default_rng(4)
     f = rng.standard_normal((B, pr.SEG)).astype(np.float32)
+    L = rng.uniform(0.0, 3.0, size=(B, K)).astype(np.float32)
     code = rng.integers(0, C, B).astype(np.int32)
     bin_ = rng.integers(0, K, B).astype(np.int32)
     code[rng.uniform(size=B) < 0.3] = -1
     bin_[code < 0] = -1
     present = (code >= 0).astype(float)
-    d_f = torch.from_numpy(f).cuda()
+    d_f = torch.from_numpy(np.concatenate([f, L], axis=1)).cuda()
     d_c = torch.from_numpy(code).cuda()
     d_b = torch.from_numpy(bin_).cuda()
     zc = torch.empty(B * C, device="cuda")
@@ -71,7 +104,7 @@ def test_logits_and_gradients_match_oracle(torch_cuda):
     st = torch.cuda.current_stream()
     net.logits(st.cuda_stream, d_f.data_ptr(), B, False, zc.data_ptr(), zb.data_ptr(), zp.data_ptr())
     st.synchronize()
-    _, rc, rb, rp = pr.forward(p, f.astype(np.float64))
+    _, rc, rb, rp = pr.forward(p, f.astype(np.float64), L.astype(np.float64))
     np.testing.assert_allclose(zc.cpu().numpy().reshape(B, C), rc, rtol=1e-4, atol=1e-4)
     np.testing.assert_allclose(zb.cpu().numpy().reshape(B, K), rb, rtol=1e-4, atol=1e-4)
     np.testing.assert_allclose(zp.cpu().numpy(), rp, rtol=1e-4, atol=1e-4)
@@ -85,10 +118,12 @@ def test_logits_and_gradients_match_oracle(torch_cuda):
     grad = torch.zeros(net.n_params, device="cuda")
     net.loss_grad(st.cuda_stream, d_f.data_ptr(), d_c.data_ptr(), d_b.data_ptr(), B, loss.data_ptr(), grad.data_ptr())
     st.synchronize()
-    ref_loss = pr.loss(p, f.astype(np.float64), np.maximum(code, 0), np.maximum(bin_, 0), present)
+    ref_loss = pr.loss(p, f.astype(np.float64), np.maximum(code, 0), np.maximum(bin_, 0), present,
+                       L.astype(np.float64))
     assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-5)
     g = pr.unflatten(grad.cpu().numpy().astype(np.float64), C, K)
-    ref = pr.grads(p, f.astype(np.float64), np.maximum(code, 0), np.maximum(bin_, 0), present)
+    ref = pr.grads(p, f.astype(np.float64), np.maximum(code, 0), np.maximum(bin_, 0), present,
+                   L.astype(np.float64))
     for k in pr.PARAM_ORDER:
         rel = np.linalg.norm(g[k] - ref[k]) / max(np.linalg.norm(ref[k]), 1e-12)
         assert rel < 1e-4, (k, rel)
@@ -130,6 +165,7 @@ def test_training_lowers_the_loss(torch_cuda):
     for i in range(B):
         f[i, 400 * bin_[i]: 400 * bin_[i] + 200] += 2.0
         f[i, 2048 + 300 * code[i]: 2048 + 300 * code[i] + 100] += 2.0
+    f = np.concatenate([f, np.zeros((B, K), np.float32)], axis=1)  # no carrier-line evidence
     d_f, d_c, d_b = (torch.from_numpy(a).cuda() for a in (f, code, bin_))
     loss = torch.zeros(1, device="cuda")
     st = torch.cuda.current_stream()
@@ -144,15 +180,15 @@ def test_training_lowers_the_loss(torch_cuda):
     assert float(loss.item()) < 0.5 * first
 
 
-def _proposed(torch, wl, net, topk, tau, cap=256, wpl=0):
-    from paper_2005_10445_gb300.binding import DETECTION_DTYPE, Search, run_proposed
+def _proposed(torch, wl, net, topk, tau, cap=256, wpl=0, bins=False):
+    from paper_2005_10445_gb300.binding import DETECTION_DTYPE, Search, run_proposed, run_proposed_bins
     s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len, windows_per_launch=wpl)
     x = torch.from_numpy(wl.iq().copy()).cuda()
     out = torch.zeros(cap * 32, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
     st = torch.cuda.current_stream()
-    nfb = run_proposed(s, net, st.cuda_stream, x.data_ptr(), wl.n_samples, topk, tau, out.data_ptr(), cap,
-                       cnt.data_ptr())
+    fn = run_proposed_bins if bins else run_proposed
+    nfb = fn(s, net, st.cuda_stream, x.data_ptr(), wl.n_samples, topk, tau, out.data_ptr(), cap, cnt.data_ptr())
     n = int(cnt.item())
     got = out.cpu().numpy().view(DETECTION_DTYPE)[: min(n, cap)].copy()
     ref, n_ref, _ = s.run(x, capacity=cap)
@@ -195,7 +231,7 @@ def test_checkpoint_resume_is_exact_and_corruption_is_refused(torch_cuda, tmp_pa
     from paper_2005_10445_gb300.binding import AtlasError, Proposal
     C, K, B = 5, 4, 16
     rng = np.random.default_rng(21)
-    f = torch.from_numpy(rng.standard_normal((B, pr.SEG)).astype(np.float32)).cuda()
+    f = torch.from_numpy(rng.standard_normal((B, pr.SEG + K)).astype(np.float32)).cuda()
     code = torch.from_numpy(rng.integers(0, C, B).astype(np.int32)).cuda()
     bin_ = torch.from_numpy(rng.integers(0, K, B).astype(np.int32)).cuda()
     loss = torch.zeros(1, device="cuda")
@@ -219,7 +255,7 @@ def test_checkpoint_resume_is_exact_and_corruption_is_refused(torch_cuda, tmp_pa
 
     raw = open(path, "rb").read()
     magic, ver, nc, nb, crc, n, step = struct.unpack("<8sIiiIqq", raw[:40])
-    assert (magic, ver, nc, nb, n, step) == (b"ATLPROP1", 1, C, K, a.n_params, 4)
+    assert (magic, ver, nc, nb, n, step) == (b"ATLPROP1", 2, C, K, a.n_params, 4)
     assert len(raw) == 40 + 3 * 4 * n and crc == zlib.crc32(raw[40:])
     before = b.get_params().tobytes()
     bad = bytearray(raw)
@@ -232,3 +268,40 @@ def test_checkpoint_resume_is_exact_and_corruption_is_refused(torch_cuda, tmp_pa
     with pytest.raises(AtlasError):
         Proposal(C + 1, K, 0).load(path)
     assert b.get_params().tobytes() == before
+
+
+@pytest.mark.parametrize("wpl", [0, 1])
+def test_bin_proposals_covering_every_bin_equal_exhaustive(torch_cuda, wpl):
+    """Bin proposals naming every bin, no fallback: every code in every bin is
+    listed, so the records equal the exhaustive search's bit for bit."""
+    from paper_2005_10445_gb300.binding import Proposal
+    wl = synth.small(seed=12, N=8192)
+    net = Proposal(len(wl.chips), len(wl.freqs_hz), 2)
+    got, n, ref, n_ref, nfb = _proposed(torch_cuda, wl, net, topk=len(wl.freqs_hz), tau=0.0, wpl=wpl, bins=True)
+    assert nfb == 0 and n == n_ref >= 3 and got.tobytes() == ref.tobytes()
+
+
+def test_bin_proposals_on_the_tags_bins_find_the_tags(torch_cuda):
+    """A network whose bin head is driven by the carrier-line features alone
+    (every weight zero but a = 1): each confident window searches every code in
+    its top two bins; every injected tag is still found, with the exhaustive
+    search's record, and fewer cells are searched than bins exist."""
+    torch = torch_cuda
+    from paper_2005_10445_gb300.binding import Proposal
+    wl = synth.small(seed=12, N=8192, snr_range=(2.0, 8.0))
+    C, K = len(wl.chips), len(wl.freqs_hz)
+    net = Proposal(C, K, 2)
+    p = {k: np.zeros(v) for k, v in pr.param_shapes(C, K).items()}
+    p["wl"] = np.array([8.0, 0.0])
+    net.set_params(pr.flatten(p).astype(np.float32))
+    got, n, ref, n_ref, nfb = _proposed(torch, wl, net, topk=2, tau=0.0, bins=True)
+    assert nfb == 0
+    key = lambda d: (int(d["code"]), int(d["window"]), int(d["lag"]), int(d["freq_bin"]))
+    by_ref = {key(d): d.tobytes() for d in ref}
+    found = {key(d): d.tobytes() for d in got}
+    for t in wl.tags:
+        N = wl.fft_len
+        hop = N - len(wl.chips[t.code]) * wl.sps
+        w = min(int(t.delay) // hop, (wl.n_samples - N + hop - 1) // hop)  # the last window is W - 1
+        k = (t.code, w, int(t.delay) - w * hop, t.bin)
+        assert k in by_ref and k in found and found[k] == by_ref[k]
