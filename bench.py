@@ -241,7 +241,12 @@ SECONDS = 1.0  # stream length of the realistic workload (--seconds; shorter str
 
 
 def workload_name() -> str:
-    return WORKLOAD if SECONDS == 1.0 else WORKLOAD.replace("realistic: 1 s", f"realistic, shortened: {SECONDS:g} s")
+    if SECONDS == 1.0:
+        return WORKLOAD
+    S, N, hop = int(round(8e6 * SECONDS)), 131072, 65536
+    W = 1 if S <= N else (S - N + hop - 1) // hop + 1
+    return (WORKLOAD.replace("realistic: 1 s", f"realistic, shortened: {SECONDS:g} s")
+            .replace("122 windows", f"{W} windows"))
 
 
 def make_workload(seed: int):

@@ -142,12 +142,23 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
 // with i = j + 1024 m and q = m' + 16 k,
 //   corr[q] = sum_j W_1024^{jk} (W_M^{j m'} sum_m Z[j + 1024 m] W_16^{m m'}),   W = exp(+2 pi i / .)
 // Step A (whole block): thread t loads Z[j + 1024 m] = G * conj(C)/M for the
-// two columns j = t and t + 512, takes their 16-point DFTs over m, multiplies
-// output m' by W_M^{j m'} and stores it at position j of chunk m'.
+// two columns j = t and j' = 1024 - t (thread 0: 0 and 512), takes their
+// 16-point DFTs over m, multiplies output m' by W_M^{j m'} and stores it at
+// position j of chunk m'.  The code spectrum of +/-1 chips is Hermitian,
+// D[M - i] = conj(D[i]), and M - (j + 1024 m) = j' + 1024 (15 - m), so column
+// j' takes column j's code spectrum in reverse order, conjugated: the thread
+// loads one column of D instead of two.  Its twiddles are
+// W_M^{j' m'} = W_16^{m'} conj(W_M^{j m'}); the W_16^{m'} factor is a cyclic
+// shift of the DFT's inputs by one (free), so column j' reuses column j's
+// twiddle, conjugated.  Columns 0 and 512 are each their own mirror.
 // Step B (warp w alone): chunk w is an independent 1024-point inverse DFT,
 // taken as two radix-32 Stockham passes through the chunk's own shared memory
-// (only __syncwarp between them), then |.|^2, the floor sum and the argmax
-// over the lags q = w + 16 k.
+// (only __syncwarp between them; the transpose is written as 16-byte pairs and
+// the second pass's twiddles W_1024^{lane r} are read from the lane's row of a
+// table as 16-byte pairs), then |.|^2, the floor sum and the argmax over the
+// lags q = w + 16 k, k = lane + 32 r.  When hop <= N/2 no valid lag has r >= 16:
+// the second pass then forms only its outputs r < 16, and the floor's sum over
+// all lags comes from that pass's inputs by Parseval (sum |X|^2 = 32 sum |x|^2).
 // A block meets only twice per item: before step A writes the chunks (the
 // previous item's chunks are read) and after (the chunks are complete).  In
 // between, warps run out of step: one warp's shared-memory traffic, global
@@ -156,12 +167,28 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
 // ---------------------------------------------------------------------------
 
 constexpr int kDifChunk = 1024;                          // points per warp transform
-constexpr int kDifChunkPad = kDifChunk + kDifChunk / 32;  // padded chunk pitch (float2)
+constexpr int kDifChunkPad = kDifChunk + kDifChunk / 16;  // chunk pitch (float2): 2 pad elements per 32
+constexpr int kDifTwPitch = 34;                          // row pitch of the step-B twiddle table
 constexpr int kDifChunks = 16;                           // M = 2^14 = 16 chunks
 constexpr int kDifThreads = 512;
 
 constexpr size_t dif_smem() {
-  return sizeof(float2) * ((size_t)kDifChunks * kDifChunkPad + TwTables<14>::N + 1024) + 2 * kDifChunks * sizeof(float4);
+  return sizeof(float2) * ((size_t)kDifChunks * kDifChunkPad + TwTables<14>::N + 32 * kDifTwPitch) +
+         2 * kDifChunks * sizeof(float4);
+}
+
+// position of point j in a chunk: two pad elements after every 32, so that
+// both a warp's 32 consecutive points and the 16-byte stores of step B's
+// transpose (rows of 32 at a pitch of 34) are free of bank conflicts
+__device__ __forceinline__ int dif_pos(int j) { return j + 2 * (j >> 5); }
+
+// W_1024^{l r} (forward) at [34 l + r], l, r < 32: a thread reads its row as 16-byte pairs
+template <int LOGM>
+__device__ __forceinline__ void build_dif_tw(float2* tw) {
+  for (int i = threadIdx.x; i < 32 * kDifTwPitch; i += blockDim.x) {
+    const int l = i / kDifTwPitch, r = i % kDifTwPitch;
+    if (r < 32) tw[TwTables<LOGM>::N + i] = twiddle<LOGM, -1>(tw, ((l * r) & 1023) << (LOGM - 10));
+  }
 }
 
 __device__ __forceinline__ void warp_reduce_stats(float& sum, float& best, int& bt) {
@@ -181,15 +208,16 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   float2* sm_tw = sm + kDifChunks * kDifChunkPad;
-  const float2* t32 = sm_tw + TwTables<LOGM>::N;  // W_1024^{a b} at [32 b + a] (forward)
-  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + 1024);  // [2][16]
+  const float2* trow = sm_tw + TwTables<LOGM>::N + kDifTwPitch * (threadIdx.x & 31);  // W_1024^{lane r}
+  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + 32 * kDifTwPitch);  // [2][16]
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int jb = t ? 1024 - t : 512;  // the thread's second column
   const int sps = p.sps;
+  const bool half = 2 * p.hop <= p.N;  // no valid lag in the upper half of any row
   load_tables<LOGM>(sm_tw, p.tw);
   __syncthreads();
-  build_tw32<LOGM>(sm_tw);
-
+  build_dif_tw<LOGM>(sm_tw);
 
   const int64_t n_items = p.pairs ? (int64_t)p.n_pairs * sps : (int64_t)sps * p.K * p.nw * p.Cg;
   int64_t prev_out = -1;
@@ -223,26 +251,43 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
       qlim = (nvalid - rho + sps - 1) / sps;
       const float2* G = p.G + row * (1 << LOGM);
       const float2* D = p.D + (int64_t)c * (1 << LOGM);
-      // step A: the two columns' 16-point DFTs and the twiddles of the split
+      // step A: the two columns' 16-point DFTs and the twiddles of the split.
+      // a[] first holds the code spectrum of column t (thread 0: column 512,
+      // the mirror of its second column), read back reversed and conjugated
+      // for column jb; b[] takes its products one slot ahead (the W_16 shift)
+      const int jd = t ? t : 512;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        a[m] = cmul(G[t + 1024 * m], D[t + 1024 * m]);
-        b[m] = cmul(G[t + 512 + 1024 * m], D[t + 512 + 1024 * m]);
+      for (int m = 0; m < 16; ++m) a[m] = D[jd + 1024 * m];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) b[(m + 1) & 15] = cmul_conj(G[jb + 1024 * m], a[15 - m]);
+      if (t == 0) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) a[m] = D[1024 * m];
       }
+#pragma unroll
+      for (int m = 0; m < 16; ++m) a[m] = cmul(G[t + 1024 * m], a[m]);
       dft_reg<16, +1>(a);
       dft_reg<16, +1>(b);
-      // output m' times W_M^{j m'}: W_M^{t m'} from the tables every eighth m'
-      // and by repeated multiplication between; W_M^{(t + 512) m'} = W_M^{t m'} W_32^{m'}
+      // output m' times W_M^{t m'} (column t) and conj(W_M^{t m'}) (column
+      // 1024 - t, after the shift): W_M^{t m'} from the tables every eighth m'
+      // and by repeated multiplication between
       const float2 wt1 = twiddle<LOGM, +1>(sm_tw, t);
       float2 wt = wt1;
 #define ATLAS_DIF_TW(M_)                                                                         \
   if (M_ > 1) wt = ((M_)&7) == 0 ? twiddle<LOGM, +1>(sm_tw, t * (M_)) : cmul(wt, wt1);            \
   a[M_] = cmul(a[M_], wt);                                                                       \
-  b[M_] = cmul(b[M_], cmul(wt, make_float2(Tw<M_, 32, +1>::re, Tw<M_, 32, +1>::im)));
+  b[M_] = cmul_conj(b[M_], wt);
       ATLAS_DIF_TW(1) ATLAS_DIF_TW(2) ATLAS_DIF_TW(3) ATLAS_DIF_TW(4) ATLAS_DIF_TW(5) ATLAS_DIF_TW(6)
       ATLAS_DIF_TW(7) ATLAS_DIF_TW(8) ATLAS_DIF_TW(9) ATLAS_DIF_TW(10) ATLAS_DIF_TW(11) ATLAS_DIF_TW(12)
       ATLAS_DIF_TW(13) ATLAS_DIF_TW(14) ATLAS_DIF_TW(15)
 #undef ATLAS_DIF_TW
+      if (t == 0) {  // column 512: W_M^{512 m'} = W_32^{m'}, i.e. W_32^{-m'} after the shift
+#define ATLAS_DIF_TW0(M_) b[M_] = cmul(b[M_], make_float2(Tw<M_, 32, -1>::re, Tw<M_, 32, -1>::im));
+        ATLAS_DIF_TW0(1) ATLAS_DIF_TW0(2) ATLAS_DIF_TW0(3) ATLAS_DIF_TW0(4) ATLAS_DIF_TW0(5)
+        ATLAS_DIF_TW0(6) ATLAS_DIF_TW0(7) ATLAS_DIF_TW0(8) ATLAS_DIF_TW0(9) ATLAS_DIF_TW0(10)
+        ATLAS_DIF_TW0(11) ATLAS_DIF_TW0(12) ATLAS_DIF_TW0(13) ATLAS_DIF_TW0(14) ATLAS_DIF_TW0(15)
+#undef ATLAS_DIF_TW0
+      }
     }
     __syncthreads();  // (1) the previous item's chunks are read and its partial results written
     if (prev_out >= 0 && warp == 0) {
@@ -256,8 +301,8 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
     if (!have) break;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-      sm[m * kDifChunkPad + t + (t >> 5)] = a[m];
-      sm[m * kDifChunkPad + t + 512 + ((t + 512) >> 5)] = b[m];
+      sm[m * kDifChunkPad + dif_pos(t)] = a[m];
+      sm[m * kDifChunkPad + dif_pos(jb)] = b[m];
     }
     __syncthreads();  // (2) every chunk is complete
 
@@ -265,48 +310,63 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
     float2* ch = sm + warp * kDifChunkPad;
     float2 x[32];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) x[r] = ch[lane + 33 * r];
+    for (int r = 0; r < 32; ++r) x[r] = ch[dif_pos(lane + 32 * r)];
     __syncwarp();
     dft_reg<32, +1>(x);
+    // transpose: point 32 lane + r, as 16-byte pairs (r, r + 1)
+    float4* row = reinterpret_cast<float4*>(ch + dif_pos(32 * lane));
 #pragma unroll
-    for (int r = 0; r < 32; ++r) ch[33 * lane + r] = x[r];
+    for (int r = 0; r < 32; r += 2) row[r / 2] = make_float4(x[r].x, x[r].y, x[r + 1].x, x[r + 1].y);
     __syncwarp();
+    const float4* tw2 = reinterpret_cast<const float4*>(trow);
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      x[r] = ch[lane + 33 * r];
-      if (r > 0) {
-        float2 w = t32[32 * r + lane];
-        w.y = -w.y;
-        x[r] = cmul(x[r], w);
-      }
+    for (int r = 0; r < 32; r += 2) {
+      const float4 w = tw2[r / 2];  // W_1024^{lane r}, W_1024^{lane (r + 1)} (forward: conjugated here)
+      x[r] = ch[dif_pos(lane + 32 * r)];
+      x[r + 1] = ch[dif_pos(lane + 32 * (r + 1))];
+      if (r > 0) x[r] = cmul_conj(x[r], make_float2(w.x, w.y));
+      x[r + 1] = cmul_conj(x[r + 1], make_float2(w.z, w.w));
     }
-    dft_reg<32, +1>(x);
     // epilogue: lag tau = sps q + rho with q = warp + 16 (lane + 32 r), increasing in r
-    float s0 = 0.f, s1 = 0.f, best = -1.f;
+    float sum, best = -1.f;
     int bq = 0x7fffffff;
     const int q0 = warp + 16 * lane;
-    if (q0 + 16 * 32 * 31 < qlim) {  // every lag of this thread is valid
+    auto argmax = [&](auto nr, bool all_valid) {
 #pragma unroll
-      for (int r = 0; r < 32; ++r) {
+      for (int r = 0; r < decltype(nr)::value; ++r) {
         const float P = fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
-        if (r & 1) s1 += P; else s0 += P;
-        if (P > best) {
+        if ((all_valid || q0 + 512 * r < qlim) && P > best) {
           best = P;
           bq = q0 + 512 * r;
         }
       }
+    };
+    if (half) {
+      // hop <= N/2: every valid lag has r < 16.  The floor's sum over all
+      // lags comes from the DFT's inputs (Parseval: sum |X_r|^2 = 32 sum |x_r|^2)
+      // and only the outputs r < 16 are formed
+      float e0 = 0.f, e1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < 32; r += 2) {
+        e0 = fmaf(x[r].x, x[r].x, fmaf(x[r].y, x[r].y, e0));
+        e1 = fmaf(x[r + 1].x, x[r + 1].x, fmaf(x[r + 1].y, x[r + 1].y, e1));
+      }
+      sum = 32.f * (e0 + e1);
+      dft_reg_low<32, +1>(x);
+      if (q0 + 512 * 15 < qlim) argmax(std::integral_constant<int, 16>{}, true);
+      else argmax(std::integral_constant<int, 16>{}, false);
     } else {
+      dft_reg<32, +1>(x);
+      float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        const float P = fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
-        if (r & 1) s1 += P; else s0 += P;
-        if (q0 + 512 * r < qlim && P > best) {
-          best = P;
-          bq = q0 + 512 * r;
-        }
+      for (int r = 0; r < 32; r += 2) {
+        s0 += fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
+        s1 += fmaf(x[r + 1].x, x[r + 1].x, x[r + 1].y * x[r + 1].y);
       }
+      sum = s0 + s1;
+      if (q0 + 512 * 31 < qlim) argmax(std::integral_constant<int, 32>{}, true);
+      else argmax(std::integral_constant<int, 32>{}, false);
     }
-    float sum = s0 + s1;
     int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
     warp_reduce_stats(sum, best, bt);
     if (lane == 0) red[par * kDifChunks + warp] = make_float4(sum, best, __int_as_float(bt), 0.f);

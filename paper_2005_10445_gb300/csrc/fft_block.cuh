@@ -75,6 +75,10 @@ struct Tw {
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+// a * conj(b)
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -(a.x * b.y)));
+}
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
 // ---------------------------------------------------------------------------
@@ -133,6 +137,44 @@ __device__ __forceinline__ void dft_reg(float2* v) {
     brev_perm<R>(v, std::make_integer_sequence<int, R>{});
     dit_stages<R, DIR, 2>(v);
   }
+}
+
+// The first R/2 outputs only: every stage but the last, then the last stage's
+// a + w b halves (the same operations as in bfly, so these outputs equal
+// dft_reg's bit for bit); v[R/2 ..] is left undefined.
+template <int DIR, int LEN, int K>
+__device__ __forceinline__ void bfly_sum(float2& a, const float2& b) {
+  if constexpr (K != 0 && 4 * K != LEN) {
+    constexpr float wr = Tw<K, LEN, DIR>::re;
+    constexpr float wi = Tw<K, LEN, DIR>::im;
+    a = make_float2(fmaf(b.x, wr, fmaf(-b.y, wi, a.x)), fmaf(b.x, wi, fmaf(b.y, wr, a.y)));
+  } else if constexpr (K == 0) {
+    a = __fadd2_rn(a, b);
+  } else {
+    const float2 t = (DIR < 0) ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);
+    a = make_float2(a.x + t.x, a.y + t.y);
+  }
+}
+
+template <int R, int DIR, int LEN>
+__device__ __forceinline__ void dit_stages_below(float2* v) {
+  if constexpr (LEN < R) {
+    dit_stage<R, DIR, LEN>(v, std::make_integer_sequence<int, LEN / 2>{});
+    dit_stages_below<R, DIR, LEN * 2>(v);
+  }
+}
+
+template <int R, int DIR, int... Ks>
+__device__ __forceinline__ void last_stage_low(float2* v, std::integer_sequence<int, Ks...>) {
+  (bfly_sum<DIR, R, Ks>(v[Ks], v[Ks + R / 2]), ...);
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dft_reg_low(float2* v) {
+  static_assert(R >= 2, "at least one stage");
+  brev_perm<R>(v, std::make_integer_sequence<int, R>{});
+  dit_stages_below<R, DIR, 2>(v);
+  last_stage_low<R, DIR>(v, std::make_integer_sequence<int, R / 2>{});
 }
 
 // ---------------------------------------------------------------------------
