@@ -13,6 +13,11 @@
 //                                   spectrum, takes one radix-2 decimation-in-frequency step
 //                                   and inverse-transforms one half: block h produces the
 //                                   lags q = 2k + h
+//   k_corr_dif<14, SPLIT>           the default correlation for M = 2^14 (one block per
+//                                   item, warp-private second and third passes) and, with
+//                                   SPLIT, for M = 2^15: each half h of k_corr_split's
+//                                   decomposition as one 2^14-point item, its input formed
+//                                   as E A_h + O B_h from three precomputed code tables
 // Section 4.1 computes cross-correlations with FFTs; the split forms are the
 // same transforms with one radix-2 stage folded into the global loads, so
 // transforms of 2^15 points need no more shared memory than 2^14.
@@ -202,9 +207,13 @@ __device__ __forceinline__ void warp_reduce_stats(float& sum, float& best, int& 
   }
 }
 
-template <int LOGM>
+// SPLIT: the rows hold 2^15-point spectra as [E | O] (k_window_fft_split) and
+// item h = 0, 1 of a (cell, rho) takes the lags q = 2 q' + h as the 2^14-point
+// inverse transform of Y_h = E A_h + O B_h (the code tables D3, k_code_split_tables).
+template <int LOGM, bool SPLIT = false>
 __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
   static_assert(LOGM == 14, "16 chunks of 1024 points");
+  constexpr int H = 1 << LOGM;
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   float2* sm_tw = sm + kDifChunks * kDifChunkPad;
@@ -219,17 +228,19 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
   __syncthreads();
   build_dif_tw<LOGM>(sm_tw);
 
-  const int64_t n_items = p.pairs ? (int64_t)p.n_pairs * sps : (int64_t)sps * p.K * p.nw * p.Cg;
+  const int64_t n_items = (SPLIT ? 2 : 1) * (p.pairs ? (int64_t)p.n_pairs * sps : (int64_t)sps * p.K * p.nw * p.Cg);
   int64_t prev_out = -1;
   int par = 0;
   for (int64_t item = blockIdx.x;; item += gridDim.x) {
     const bool have = item < n_items;
     int64_t out = 0;
-    int rho = 0, qlim = 0;
+    int rho = 0, qlim = 0, h = 0;
     float2 a[16], b[16];
     if (have) {
-      rho = (int)(item % sps);
-      const int64_t rest = item / sps;
+      const int64_t it = SPLIT ? item >> 1 : item;
+      if (SPLIT) h = (int)(item & 1);
+      rho = (int)(it % sps);
+      const int64_t rest = it / sps;
       int64_t row;
       int c, w;
       if (p.pairs) {
@@ -249,8 +260,12 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
       }
       const int nvalid = valid_lags(p, w);
       qlim = (nvalid - rho + sps - 1) / sps;
-      const float2* G = p.G + row * (1 << LOGM);
-      const float2* D = p.D + (int64_t)c * (1 << LOGM);
+      if (SPLIT) {  // lags q = 2 q' + h: count the q' with 2 q' + h < qlim
+        qlim = qlim > h ? (qlim - h + 1) >> 1 : 0;
+        out = 2 * out + h;
+      }
+      const float2* G = p.G + row * (SPLIT ? 2 * H : H);
+      const float2* D = SPLIT ? p.D3 + ((int64_t)c * 3 + (h ? 2 : 0)) * H : p.D + (int64_t)c * H;
       // step A: the two columns' 16-point DFTs and the twiddles of the split.
       // a[] first holds the code spectrum of column t (thread 0: column 512,
       // the mirror of its second column), read back reversed and conjugated
@@ -266,6 +281,21 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
       }
 #pragma unroll
       for (int m = 0; m < 16; ++m) a[m] = cmul(G[t + 1024 * m], a[m]);
+      if (SPLIT) {  // + O B_h: the second table, read the same way
+        const float2* O = G + H;
+        const float2* B = p.D3 + ((int64_t)c * 3 + (h ? 0 : 1)) * H;
+        float2 d[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) d[m] = B[jd + 1024 * m];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) b[(m + 1) & 15] = cfma_conj(b[(m + 1) & 15], O[jb + 1024 * m], d[15 - m]);
+        if (t == 0) {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) d[m] = B[1024 * m];
+        }
+#pragma unroll
+        for (int m = 0; m < 16; ++m) a[m] = cfma(a[m], O[t + 1024 * m], d[m]);
+      }
       dft_reg<16, +1>(a);
       dft_reg<16, +1>(b);
       // output m' times W_M^{t m'} (column t) and conj(W_M^{t m'}) (column
@@ -367,7 +397,7 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
       if (q0 + 512 * 31 < qlim) argmax(std::integral_constant<int, 32>{}, true);
       else argmax(std::integral_constant<int, 32>{}, false);
     }
-    int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
+    int bt = bq == 0x7fffffff ? bq : (SPLIT ? 2 * bq + h : bq) * sps + rho;
     warp_reduce_stats(sum, best, bt);
     if (lane == 0) red[par * kDifChunks + warp] = make_float4(sum, best, __int_as_float(bt), 0.f);
     prev_out = out;
@@ -475,9 +505,12 @@ struct FftLaunch {
 
   static cudaError_t prepare() {
     cudaError_t e;
-    void (*dif)(CorrParams) = k_corr_dif<14>;
+    void (*dif)(CorrParams) = k_corr_dif<14, false>;
+    void (*dif_split)(CorrParams) = k_corr_dif<14, true>;
     if (LOGE == 5 &&
-        (e = cudaFuncSetAttribute(dif, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dif_smem())) != cudaSuccess)
+        ((e = cudaFuncSetAttribute(dif, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dif_smem())) != cudaSuccess ||
+         (e = cudaFuncSetAttribute(dif_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dif_smem())) !=
+             cudaSuccess))
       return e;
     if ((e = prepare_one<10>()) != cudaSuccess) return e;
     if ((e = prepare_one<11>()) != cudaSuccess) return e;
@@ -540,6 +573,7 @@ struct FftLaunch {
     if (p.pairs && (split || logM > 14)) return cudaErrorInvalidValue;  // listed cells: single-block sizes
     dim3 grid(p.sps, p.pairs ? 1 : p.K, p.pairs ? p.n_pairs : p.nw * p.Cg);
     dim3 g2(2 * p.sps, p.K, p.nw * p.Cg);
+    if (split && LOGE == 5 && logM == 15 && p.D3) return corr_dif<true>(p, s);
     if (split) {
       switch (logM) {
         case 14: k_corr_split<13, LOGE><<<g2, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
@@ -548,7 +582,7 @@ struct FftLaunch {
       }
       return cudaGetLastError();
     }
-    if (LOGE == 5 && logM == 14) return corr_dif(p, s);
+    if (LOGE == 5 && logM == 14) return corr_dif<false>(p, s);
     switch (logM) {
       case 10: return corr_persistent<10>(p, s);
       case 11: return corr_persistent<11>(p, s);
@@ -559,17 +593,19 @@ struct FftLaunch {
     }
   }
 
-  // k_corr_dif with as many blocks as fit on the device at once (at most one per cell)
+  // k_corr_dif with as many blocks as fit on the device at once (at most one per item)
+  template <bool SPLIT>
   static cudaError_t corr_dif(const CorrParams& p, cudaStream_t s) {
     static int resident = 0;
     if (resident == 0) {
-      void (*kern)(CorrParams) = k_corr_dif<14>;
+      void (*kern)(CorrParams) = k_corr_dif<14, SPLIT>;
       const cudaError_t e = resident_blocks(kern, kDifThreads, dif_smem(), &resident);
       if (e != cudaSuccess) return e;
     }
-    const int64_t items = p.pairs ? (int64_t)p.n_pairs * p.sps : (int64_t)p.sps * p.K * p.nw * p.Cg;
+    const int64_t items = (SPLIT ? 2 : 1) *
+                          (p.pairs ? (int64_t)p.n_pairs * p.sps : (int64_t)p.sps * p.K * p.nw * p.Cg);
     const unsigned blocks = (unsigned)std::min<int64_t>(items, resident);
-    k_corr_dif<14><<<blocks, kDifThreads, dif_smem(), s>>>(p);
+    k_corr_dif<14, SPLIT><<<blocks, kDifThreads, dif_smem(), s>>>(p);
     return cudaGetLastError();
   }
 

@@ -42,6 +42,10 @@ struct WindowFftParams {
 struct CorrParams {
   const float2* G;          // [nw][K][sps][M]
   const float2* D;          // [Cg][M] conj(FFT_M(chips)) / M
+  // M = 2^15 only: per code the three half-length tables of the split
+  // correlation, [Cg][3][M/2] = {D[i] + D[i + M/2], W^i (D[i] - D[i + M/2]),
+  // W^-i (D[i] - D[i + M/2])}, W = exp(-2 pi i / M) (null: not built)
+  const float2* D3 = nullptr;
   const float2* tw;         // twiddle tables of the block transform
   const float2* tw2 = nullptr;  // tables of the full size M (split transforms only)
   float4* part;             // out [nw][Cg][K][sps] (x2 for split) = {sum P, P*, tau*, 0}
@@ -99,6 +103,7 @@ struct CodeBankParams {
   const int* n_chips;       // [Cg]
   const float2* tw;
   float2* D;                // [Cg][M]
+  float2* D3 = nullptr;     // M = 2^15: [Cg][3][M/2] tables of the split correlation (see CorrParams)
   int M;
   float scale;              // 1 / M
 };

@@ -101,6 +101,28 @@ __global__ void k_code_bank_combine(float2* D, int H, int n_codes, float scale) 
   Dc[k + H] = make_float2((e.x - o.x) * scale, -(e.y - o.y) * scale);
 }
 
+// The split correlation of 2^15 points takes the lags q = 2k + h as two
+// half-length inverse transforms of Y_h (radix-2 decimation in frequency).
+// With G[i] = E[i] + W^i O[i], G[i + H] = E[i] - W^i O[i] and Z = G D:
+//   Y_0[i] = Z[i] + Z[i + H]          = E[i] Dp[i] + O[i] W^i Dm[i]
+//   Y_1[i] = (Z[i] - Z[i + H]) W^-i   = E[i] W^-i Dm[i] + O[i] Dp[i]
+// (Dp = D[i] + D[i + H], Dm = D[i] - D[i + H], W = exp(-2 pi i / 2H)), so the
+// three code tables below make each output a sum of two products.
+__global__ void k_code_split_tables(const float2* D, float2* D3, int H, int n_codes) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)H * n_codes) return;
+  const int c = (int)(i / H), k = (int)(i % H);
+  const float2* Dc = D + (int64_t)c * (2 * H);
+  float2* T = D3 + (int64_t)c * (3 * H);
+  double sn, cs;
+  sincospi(-(double)k / (double)H, &sn, &cs);  // W^k
+  const double px = (double)Dc[k].x + Dc[k + H].x, py = (double)Dc[k].y + Dc[k + H].y;
+  const double mx = (double)Dc[k].x - Dc[k + H].x, my = (double)Dc[k].y - Dc[k + H].y;
+  T[k] = make_float2((float)px, (float)py);
+  T[H + k] = make_float2((float)(cs * mx - sn * my), (float)(cs * my + sn * mx));
+  T[2 * H + k] = make_float2((float)(cs * mx + sn * my), (float)(cs * my - sn * mx));
+}
+
 // ---------------------------------------------------------------------------
 // mix + box sum + decimation (one read of each window for all bins)
 // ---------------------------------------------------------------------------
@@ -488,6 +510,10 @@ cudaError_t launch_code_bank(int logM, const CodeBankParams& p, int n_codes, cud
       const int H = 1 << 14;
       const int64_t n = (int64_t)H * n_codes;
       k_code_bank_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.D, H, n_codes, p.scale);
+      if (p.D3) {
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_code_split_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.D, p.D3, H, n_codes);
+      }
       break;
     }
     default: return cudaErrorInvalidValue;

@@ -69,6 +69,7 @@ struct Group {
   std::vector<int> codes;      // global code ids
   int* d_codes = nullptr;      // [Cg]
   float2* d_spec = nullptr;    // [Cg][M] conj(FFT_M(chips)) / M
+  float2* d_spec3 = nullptr;   // M = 2^15: [Cg][3][M/2] tables of the split correlation
   const float2* d_tw_full = nullptr;  // tables of M
   const float2* d_tw_half = nullptr;  // tables of M / 2
   const float2* tw() const { return split ? d_tw_half : d_tw_full; }  // tables of the block transform
@@ -173,6 +174,7 @@ void free_ctx(atlas_acq_ctx* ctx) {
   for (auto& g : ctx->groups) {
     cudaFree(g.d_codes);
     cudaFree(g.d_spec);
+    cudaFree(g.d_spec3);
   }
   for (auto& kv : ctx->d_tw) cudaFree(kv.second);
   cudaFree(ctx->d_chips);
@@ -317,6 +319,9 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
     CK(upload(&g.d_codes, g.codes.data(), g.codes.size()));
     if (cudaMalloc((void**)&g.d_spec, sizeof(float2) * (size_t)g.M * g.codes.size()) != cudaSuccess)
       return ATLAS_ERR_NO_MEMORY;
+    if (g.logM == 15 &&
+        cudaMalloc((void**)&g.d_spec3, sizeof(float2) * (size_t)3 * (g.M / 2) * g.codes.size()) != cudaSuccess)
+      return ATLAS_ERR_NO_MEMORY;
     std::vector<int64_t> goff(g.codes.size());
     std::vector<int> gn(g.codes.size());
     for (size_t i = 0; i < g.codes.size(); ++i) {
@@ -333,6 +338,7 @@ int create_impl(atlas_acq_ctx* ctx, const int8_t* chips, const int32_t* chips_pe
     p.n_chips = d_gn;
     p.tw = g.logM == 15 ? g.d_tw_half : g.d_tw_full;
     p.D = g.d_spec;
+    p.D3 = g.d_spec3;
     p.M = g.M;
     p.scale = 1.0f / (float)g.M;
     cudaError_t e = atlas::launch_code_bank(g.logM, p, (int)g.codes.size(), 0);
@@ -377,6 +383,7 @@ int launch_chunk(atlas_acq_ctx* ctx, const Group& g, cudaStream_t st, const floa
   CorrParams b;
   b.G = ctx->d_G;
   b.D = g.d_spec;
+  b.D3 = g.d_spec3;
   b.tw = g.tw();
   b.tw2 = g.d_tw_full;
   b.part = ctx->d_part;
