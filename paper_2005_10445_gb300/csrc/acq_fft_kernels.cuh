@@ -140,8 +140,10 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
 }
 
 // ---------------------------------------------------------------------------
-// k_corr_dif: the per-code correlation of M = 2^14 points with warp-private
-// second and third passes.
+// k_corr_dif: the per-code correlation of M = 2^12, 2^13 or 2^14 points with
+// warp-private second and third passes (written out below for M = 2^14; a
+// smaller M has NCH = M / 1024 chunks, NCH warps and NCH-point step-A DFTs,
+// each thread taking 16 / NCH column pairs).
 //
 // The inverse transform is split by decimation in frequency, M = 16 x 1024:
 // with i = j + 1024 m and q = m' + 16 k,
@@ -174,12 +176,18 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
 constexpr int kDifChunk = 1024;                          // points per warp transform
 constexpr int kDifChunkPad = kDifChunk + kDifChunk / 16;  // chunk pitch (float2): 2 pad elements per 32
 constexpr int kDifTwPitch = 34;                          // row pitch of the step-B twiddle table
-constexpr int kDifChunks = 16;                           // M = 2^14 = 16 chunks
-constexpr int kDifThreads = 512;
 
+// chunks of 1024 points (= warps, = points of the step-A DFT) and threads of
+// the block for a transform of 2^LOGM points
+template <int LOGM>
+constexpr int dif_chunks() { return 1 << (LOGM - 10); }
+template <int LOGM>
+constexpr int dif_threads() { return 32 * dif_chunks<LOGM>(); }
+
+template <int LOGM>
 constexpr size_t dif_smem() {
-  return sizeof(float2) * ((size_t)kDifChunks * kDifChunkPad + TwTables<14>::N + 32 * kDifTwPitch) +
-         2 * kDifChunks * sizeof(float4);
+  return sizeof(float2) * ((size_t)dif_chunks<LOGM>() * kDifChunkPad + TwTables<LOGM>::N + 32 * kDifTwPitch) +
+         2 * dif_chunks<LOGM>() * sizeof(float4);
 }
 
 // position of point j in a chunk: two pad elements after every 32, so that
@@ -207,21 +215,55 @@ __device__ __forceinline__ void warp_reduce_stats(float& sum, float& best, int& 
   }
 }
 
-// SPLIT: the rows hold 2^15-point spectra as [E | O] (k_window_fft_split) and
-// item h = 0, 1 of a (cell, rho) takes the lags q = 2 q' + h as the 2^14-point
-// inverse transform of Y_h = E A_h + O B_h (the code tables D3, k_code_split_tables).
+// Step A's twiddles for output m' = MP of the column pair (j, 1024 - j):
+// W_M^{j m'} for column j and its conjugate for the mirror column (after the
+// shift of its DFT inputs); W_M^{j m'} from the tables every eighth m' and by
+// repeated multiplication between.
+template <int LOGM, int MP>
+__device__ __forceinline__ void dif_twiddle_one(float2* a, float2* b, float2& wt, const float2& wt1,
+                                                const float2* tw, int j) {
+  if constexpr (MP > 1) wt = (MP & 7) == 0 ? twiddle<LOGM, +1>(tw, j * MP) : cmul(wt, wt1);
+  a[MP] = cmul(a[MP], wt);
+  b[MP] = cmul_conj(b[MP], wt);
+}
+
+template <int LOGM, int... Ms>
+__device__ __forceinline__ void dif_twiddles(float2* a, float2* b, const float2* tw, int j,
+                                             std::integer_sequence<int, Ms...>) {
+  const float2 wt1 = twiddle<LOGM, +1>(tw, j);
+  float2 wt = wt1;
+  (dif_twiddle_one<LOGM, Ms + 1>(a, b, wt, wt1, tw, j), ...);
+}
+
+// column 512 (the mirror of itself): W_M^{512 m'} = W_{2 NCH}^{m'}, i.e.
+// W_{2 NCH}^{-m'} after the shift by W_NCH^{m'}
+template <int NCH, int... Ms>
+__device__ __forceinline__ void dif_twiddle_col512(float2* b, std::integer_sequence<int, Ms...>) {
+  ((b[Ms + 1] = cmul(b[Ms + 1], make_float2(Tw<Ms + 1, 2 * NCH, -1>::re, Tw<Ms + 1, 2 * NCH, -1>::im))), ...);
+}
+
+// One block of 32 NCH threads per item (NCH = M / 1024 chunks, one warp per
+// chunk in step B).  Thread t takes the column pairs (j, 1024 - j) with
+// j = t + 32 NCH i, i < 16 / NCH (the pair j = 0 is the columns 0 and 512).
+// SPLIT (M = 2^14 blocks of a 2^15-point row): the rows hold the spectra as
+// [E | O] (k_window_fft_split) and item h = 0, 1 of a (cell, rho) takes the
+// lags q = 2 q' + h as the 2^14-point inverse transform of Y_h = E A_h + O B_h
+// (the code tables D3, k_code_split_tables).
 template <int LOGM, bool SPLIT = false>
-__global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
-  static_assert(LOGM == 14, "16 chunks of 1024 points");
+__global__ void __launch_bounds__(dif_threads<LOGM>(), 16 / dif_chunks<LOGM>()) k_corr_dif(CorrParams p) {
+  constexpr int NCH = dif_chunks<LOGM>();
+  constexpr int T = 32 * NCH;
+  constexpr int NP = 512 / T;  // column pairs per thread
+  static_assert(LOGM >= 12 && LOGM <= 14, "4, 8 or 16 chunks of 1024 points");
+  static_assert(!SPLIT || LOGM == 14, "split rows: halves of 2^15 points");
   constexpr int H = 1 << LOGM;
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
-  float2* sm_tw = sm + kDifChunks * kDifChunkPad;
+  float2* sm_tw = sm + NCH * kDifChunkPad;
   const float2* trow = sm_tw + TwTables<LOGM>::N + kDifTwPitch * (threadIdx.x & 31);  // W_1024^{lane r}
-  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + 32 * kDifTwPitch);  // [2][16]
+  float4* red = reinterpret_cast<float4*>(sm_tw + TwTables<LOGM>::N + 32 * kDifTwPitch);  // [2][NCH]
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int jb = t ? 1024 - t : 512;  // the thread's second column
   const int sps = p.sps;
   const bool half = 2 * p.hop <= p.N;  // no valid lag in the upper half of any row
   load_tables<LOGM>(sm_tw, p.tw);
@@ -235,7 +277,7 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
     const bool have = item < n_items;
     int64_t out = 0;
     int rho = 0, qlim = 0, h = 0;
-    float2 a[16], b[16];
+    float2 a[NP][NCH], b[NP][NCH];
     if (have) {
       const int64_t it = SPLIT ? item >> 1 : item;
       if (SPLIT) h = (int)(item & 1);
@@ -266,63 +308,52 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
       }
       const float2* G = p.G + row * (SPLIT ? 2 * H : H);
       const float2* D = SPLIT ? p.D3 + ((int64_t)c * 3 + (h ? 2 : 0)) * H : p.D + (int64_t)c * H;
-      // step A: the two columns' 16-point DFTs and the twiddles of the split.
-      // a[] first holds the code spectrum of column t (thread 0: column 512,
-      // the mirror of its second column), read back reversed and conjugated
-      // for column jb; b[] takes its products one slot ahead (the W_16 shift)
-      const int jd = t ? t : 512;
+      // step A: each pair's two NCH-point DFTs and the twiddles of the split.
+      // a[i] first holds the code spectrum of column j (pair 0 of thread 0:
+      // column 512, the mirror of its second column), read back reversed and
+      // conjugated for column jb; b[i] takes its products one slot ahead (the
+      // W_NCH shift)
 #pragma unroll
-      for (int m = 0; m < 16; ++m) a[m] = D[jd + 1024 * m];
+      for (int i = 0; i < NP; ++i) {
+        const int j = t + T * i;
+        const bool p0 = (i == 0 && t == 0);
+        const int jb = p0 ? 512 : 1024 - j;
+        const int jd = p0 ? 512 : j;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) b[(m + 1) & 15] = cmul_conj(G[jb + 1024 * m], a[15 - m]);
-      if (t == 0) {
+        for (int m = 0; m < NCH; ++m) a[i][m] = D[jd + 1024 * m];
 #pragma unroll
-        for (int m = 0; m < 16; ++m) a[m] = D[1024 * m];
-      }
+        for (int m = 0; m < NCH; ++m) b[i][(m + 1) % NCH] = cmul_conj(G[jb + 1024 * m], a[i][NCH - 1 - m]);
+        if (p0) {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) a[m] = cmul(G[t + 1024 * m], a[m]);
-      if (SPLIT) {  // + O B_h: the second table, read the same way
-        const float2* O = G + H;
-        const float2* B = p.D3 + ((int64_t)c * 3 + (h ? 0 : 1)) * H;
-        float2 d[16];
-#pragma unroll
-        for (int m = 0; m < 16; ++m) d[m] = B[jd + 1024 * m];
-#pragma unroll
-        for (int m = 0; m < 16; ++m) b[(m + 1) & 15] = cfma_conj(b[(m + 1) & 15], O[jb + 1024 * m], d[15 - m]);
-        if (t == 0) {
-#pragma unroll
-          for (int m = 0; m < 16; ++m) d[m] = B[1024 * m];
+          for (int m = 0; m < NCH; ++m) a[i][m] = D[1024 * m];
         }
 #pragma unroll
-        for (int m = 0; m < 16; ++m) a[m] = cfma(a[m], O[t + 1024 * m], d[m]);
-      }
-      dft_reg<16, +1>(a);
-      dft_reg<16, +1>(b);
-      // output m' times W_M^{t m'} (column t) and conj(W_M^{t m'}) (column
-      // 1024 - t, after the shift): W_M^{t m'} from the tables every eighth m'
-      // and by repeated multiplication between
-      const float2 wt1 = twiddle<LOGM, +1>(sm_tw, t);
-      float2 wt = wt1;
-#define ATLAS_DIF_TW(M_)                                                                         \
-  if (M_ > 1) wt = ((M_)&7) == 0 ? twiddle<LOGM, +1>(sm_tw, t * (M_)) : cmul(wt, wt1);            \
-  a[M_] = cmul(a[M_], wt);                                                                       \
-  b[M_] = cmul_conj(b[M_], wt);
-      ATLAS_DIF_TW(1) ATLAS_DIF_TW(2) ATLAS_DIF_TW(3) ATLAS_DIF_TW(4) ATLAS_DIF_TW(5) ATLAS_DIF_TW(6)
-      ATLAS_DIF_TW(7) ATLAS_DIF_TW(8) ATLAS_DIF_TW(9) ATLAS_DIF_TW(10) ATLAS_DIF_TW(11) ATLAS_DIF_TW(12)
-      ATLAS_DIF_TW(13) ATLAS_DIF_TW(14) ATLAS_DIF_TW(15)
-#undef ATLAS_DIF_TW
-      if (t == 0) {  // column 512: W_M^{512 m'} = W_32^{m'}, i.e. W_32^{-m'} after the shift
-#define ATLAS_DIF_TW0(M_) b[M_] = cmul(b[M_], make_float2(Tw<M_, 32, -1>::re, Tw<M_, 32, -1>::im));
-        ATLAS_DIF_TW0(1) ATLAS_DIF_TW0(2) ATLAS_DIF_TW0(3) ATLAS_DIF_TW0(4) ATLAS_DIF_TW0(5)
-        ATLAS_DIF_TW0(6) ATLAS_DIF_TW0(7) ATLAS_DIF_TW0(8) ATLAS_DIF_TW0(9) ATLAS_DIF_TW0(10)
-        ATLAS_DIF_TW0(11) ATLAS_DIF_TW0(12) ATLAS_DIF_TW0(13) ATLAS_DIF_TW0(14) ATLAS_DIF_TW0(15)
-#undef ATLAS_DIF_TW0
+        for (int m = 0; m < NCH; ++m) a[i][m] = cmul(G[j + 1024 * m], a[i][m]);
+        if (SPLIT) {  // + O B_h: the second table, read the same way
+          const float2* O = G + H;
+          const float2* B = p.D3 + ((int64_t)c * 3 + (h ? 0 : 1)) * H;
+          float2 d[NCH];
+#pragma unroll
+          for (int m = 0; m < NCH; ++m) d[m] = B[jd + 1024 * m];
+#pragma unroll
+          for (int m = 0; m < NCH; ++m)
+            b[i][(m + 1) % NCH] = cfma_conj(b[i][(m + 1) % NCH], O[jb + 1024 * m], d[NCH - 1 - m]);
+          if (p0) {
+#pragma unroll
+            for (int m = 0; m < NCH; ++m) d[m] = B[1024 * m];
+          }
+#pragma unroll
+          for (int m = 0; m < NCH; ++m) a[i][m] = cfma(a[i][m], O[j + 1024 * m], d[m]);
+        }
+        dft_reg<NCH, +1>(a[i]);
+        dft_reg<NCH, +1>(b[i]);
+        dif_twiddles<LOGM>(a[i], b[i], sm_tw, j, std::make_integer_sequence<int, NCH - 1>{});
+        if (p0) dif_twiddle_col512<NCH>(b[i], std::make_integer_sequence<int, NCH - 1>{});
       }
     }
     __syncthreads();  // (1) the previous item's chunks are read and its partial results written
     if (prev_out >= 0 && warp == 0) {
-      float4 r = lane < kDifChunks ? red[(par ^ 1) * kDifChunks + lane]
-                                   : make_float4(0.f, -1.f, __int_as_float(0x7fffffff), 0.f);
+      float4 r = lane < NCH ? red[(par ^ 1) * NCH + lane] : make_float4(0.f, -1.f, __int_as_float(0x7fffffff), 0.f);
       float sum = r.x, best = r.y;
       int bt = __float_as_int(r.z);
       warp_reduce_stats(sum, best, bt);
@@ -330,9 +361,14 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
     }
     if (!have) break;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      sm[m * kDifChunkPad + dif_pos(t)] = a[m];
-      sm[m * kDifChunkPad + dif_pos(jb)] = b[m];
+    for (int i = 0; i < NP; ++i) {
+      const int j = t + T * i;
+      const int jb = (i == 0 && t == 0) ? 512 : 1024 - j;
+#pragma unroll
+      for (int m = 0; m < NCH; ++m) {
+        sm[m * kDifChunkPad + dif_pos(j)] = a[i][m];
+        sm[m * kDifChunkPad + dif_pos(jb)] = b[i][m];
+      }
     }
     __syncthreads();  // (2) every chunk is complete
 
@@ -357,17 +393,18 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
       if (r > 0) x[r] = cmul_conj(x[r], make_float2(w.x, w.y));
       x[r + 1] = cmul_conj(x[r + 1], make_float2(w.z, w.w));
     }
-    // epilogue: lag tau = sps q + rho with q = warp + 16 (lane + 32 r), increasing in r
+    // epilogue: lag tau = sps q + rho with q = warp + NCH (lane + 32 r), increasing in r
+    constexpr int QS = 32 * NCH;  // q step per r
     float sum, best = -1.f;
     int bq = 0x7fffffff;
-    const int q0 = warp + 16 * lane;
+    const int q0 = warp + NCH * lane;
     auto argmax = [&](auto nr, bool all_valid) {
 #pragma unroll
       for (int r = 0; r < decltype(nr)::value; ++r) {
         const float P = fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
-        if ((all_valid || q0 + 512 * r < qlim) && P > best) {
+        if ((all_valid || q0 + QS * r < qlim) && P > best) {
           best = P;
-          bq = q0 + 512 * r;
+          bq = q0 + QS * r;
         }
       }
     };
@@ -383,7 +420,7 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
       }
       sum = 32.f * (e0 + e1);
       dft_reg_low<32, +1>(x);
-      if (q0 + 512 * 15 < qlim) argmax(std::integral_constant<int, 16>{}, true);
+      if (q0 + QS * 15 < qlim) argmax(std::integral_constant<int, 16>{}, true);
       else argmax(std::integral_constant<int, 16>{}, false);
     } else {
       dft_reg<32, +1>(x);
@@ -394,12 +431,12 @@ __global__ void __launch_bounds__(kDifThreads, 1) k_corr_dif(CorrParams p) {
         s1 += fmaf(x[r + 1].x, x[r + 1].x, x[r + 1].y * x[r + 1].y);
       }
       sum = s0 + s1;
-      if (q0 + 512 * 31 < qlim) argmax(std::integral_constant<int, 32>{}, true);
+      if (q0 + QS * 31 < qlim) argmax(std::integral_constant<int, 32>{}, true);
       else argmax(std::integral_constant<int, 32>{}, false);
     }
     int bt = bq == 0x7fffffff ? bq : (SPLIT ? 2 * bq + h : bq) * sps + rho;
     warp_reduce_stats(sum, best, bt);
-    if (lane == 0) red[par * kDifChunks + warp] = make_float4(sum, best, __int_as_float(bt), 0.f);
+    if (lane == 0) red[par * NCH + warp] = make_float4(sum, best, __int_as_float(bt), 0.f);
     prev_out = out;
     par ^= 1;
   }
@@ -505,13 +542,18 @@ struct FftLaunch {
 
   static cudaError_t prepare() {
     cudaError_t e;
-    void (*dif)(CorrParams) = k_corr_dif<14, false>;
-    void (*dif_split)(CorrParams) = k_corr_dif<14, true>;
-    if (LOGE == 5 &&
-        ((e = cudaFuncSetAttribute(dif, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dif_smem())) != cudaSuccess ||
-         (e = cudaFuncSetAttribute(dif_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dif_smem())) !=
-             cudaSuccess))
-      return e;
+    if (LOGE == 5) {
+      void (*d12)(CorrParams) = k_corr_dif<12, false>;
+      void (*d13)(CorrParams) = k_corr_dif<13, false>;
+      void (*d14)(CorrParams) = k_corr_dif<14, false>;
+      void (*d14s)(CorrParams) = k_corr_dif<14, true>;
+      const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+      if ((e = cudaFuncSetAttribute(d12, attr, (int)dif_smem<12>())) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(d13, attr, (int)dif_smem<13>())) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(d14, attr, (int)dif_smem<14>())) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(d14s, attr, (int)dif_smem<14>())) != cudaSuccess)
+        return e;
+    }
     if ((e = prepare_one<10>()) != cudaSuccess) return e;
     if ((e = prepare_one<11>()) != cudaSuccess) return e;
     if ((e = prepare_one<12>()) != cudaSuccess) return e;
@@ -573,7 +615,7 @@ struct FftLaunch {
     if (p.pairs && (split || logM > 14)) return cudaErrorInvalidValue;  // listed cells: single-block sizes
     dim3 grid(p.sps, p.pairs ? 1 : p.K, p.pairs ? p.n_pairs : p.nw * p.Cg);
     dim3 g2(2 * p.sps, p.K, p.nw * p.Cg);
-    if (split && LOGE == 5 && logM == 15 && p.D3) return corr_dif<true>(p, s);
+    if (split && LOGE == 5 && logM == 15 && p.D3) return corr_dif<14, true>(p, s);
     if (split) {
       switch (logM) {
         case 14: k_corr_split<13, LOGE><<<g2, fft_threads<13, LOGE>(), fft_smem<13>(), s>>>(p); break;
@@ -582,7 +624,9 @@ struct FftLaunch {
       }
       return cudaGetLastError();
     }
-    if (LOGE == 5 && logM == 14) return corr_dif<false>(p, s);
+    if (LOGE == 5 && logM == 12) return corr_dif<12, false>(p, s);
+    if (LOGE == 5 && logM == 13) return corr_dif<13, false>(p, s);
+    if (LOGE == 5 && logM == 14) return corr_dif<14, false>(p, s);
     switch (logM) {
       case 10: return corr_persistent<10>(p, s);
       case 11: return corr_persistent<11>(p, s);
@@ -594,18 +638,18 @@ struct FftLaunch {
   }
 
   // k_corr_dif with as many blocks as fit on the device at once (at most one per item)
-  template <bool SPLIT>
+  template <int LOGM, bool SPLIT>
   static cudaError_t corr_dif(const CorrParams& p, cudaStream_t s) {
     static int resident = 0;
     if (resident == 0) {
-      void (*kern)(CorrParams) = k_corr_dif<14, SPLIT>;
-      const cudaError_t e = resident_blocks(kern, kDifThreads, dif_smem(), &resident);
+      void (*kern)(CorrParams) = k_corr_dif<LOGM, SPLIT>;
+      const cudaError_t e = resident_blocks(kern, dif_threads<LOGM>(), dif_smem<LOGM>(), &resident);
       if (e != cudaSuccess) return e;
     }
     const int64_t items = (SPLIT ? 2 : 1) *
                           (p.pairs ? (int64_t)p.n_pairs * p.sps : (int64_t)p.sps * p.K * p.nw * p.Cg);
     const unsigned blocks = (unsigned)std::min<int64_t>(items, resident);
-    k_corr_dif<14, SPLIT><<<blocks, kDifThreads, dif_smem(), s>>>(p);
+    k_corr_dif<LOGM, SPLIT><<<blocks, dif_threads<LOGM>(), dif_smem<LOGM>(), s>>>(p);
     return cudaGetLastError();
   }
 
