@@ -71,6 +71,13 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_window_fft(Window
     // output is written (the passes are separated by block barriers), so the
     // transform can overwrite its own input row
     float2* G = p.G + row * FFT::M;
+    // the block's next row (written by the mix kernel, in device memory) is
+    // fetched into L2 while this one is transformed, so its loads hit L2
+    if (row + gridDim.x < rows) {
+      const char* nxt = reinterpret_cast<const char*>(G + (int64_t)gridDim.x * FFT::M);
+      for (int off = 128 * (int)threadIdx.x; off < FFT::M * (int)sizeof(float2); off += 128 * (int)blockDim.x)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(nxt + off));
+    }
     auto load = [&](int i) { return G[i]; };
     auto emit = [&](int i, float2 v) { G[i] = v; };
     FFT::run(sm, sm_tw, load, emit);
