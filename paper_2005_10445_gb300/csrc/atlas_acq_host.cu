@@ -118,6 +118,8 @@ struct atlas_acq_ctx {
   // host-buffer path (allocated on first use per size, kept)
   float2* d_stage = nullptr;
   int64_t stage_samples = 0;
+  cudaStream_t copy_st = nullptr;  // the second part of the host-to-device copy
+  cudaEvent_t ev_copy_in = nullptr, ev_copy_done = nullptr;
   atlas_detection* d_stage_out = nullptr;
   int stage_cap = 0;
   int* d_stage_count = nullptr;
@@ -193,6 +195,9 @@ void free_ctx(atlas_acq_ctx* ctx) {
   if (ctx->ev_corr) cudaEventDestroy(ctx->ev_corr);
   if (ctx->ev_sel) cudaEventDestroy(ctx->ev_sel);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  if (ctx->ev_copy_in) cudaEventDestroy(ctx->ev_copy_in);
+  if (ctx->ev_copy_done) cudaEventDestroy(ctx->ev_copy_done);
+  if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
   cudaFree(ctx->d_items);
   cudaFree(ctx->d_pairs);
   cudaFree(ctx->d_pair_stats);
@@ -461,7 +466,8 @@ int launch_refine_all(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int6
 
 // only_group >= 0 restricts the search to one code-length group (autotuning).
 int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, atlas_cell* cells,
-             atlas_detection* out, int capacity, int* d_count, int only_group = -1) {
+             atlas_detection* out, int capacity, int* d_count, int only_group = -1,
+             cudaEvent_t rest_ready = nullptr) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(st, &cap));
   const bool profiling = ctx->profiling && cap == cudaStreamCaptureStatusNone;
@@ -479,11 +485,17 @@ int run_impl(atlas_acq_ctx* ctx, cudaStream_t st, const float2* x, int64_t S, at
     int wc = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g.N))));
     if (g.wc > 0) wc = std::min(wc, g.wc);
     for (int w0 = 0; w0 < W; w0 += wc) {
+      // rest_ready: only the samples of the first launch group are known to be on the device
+      if (rest_ready && !(gi == 0 && w0 == 0)) {
+        CK(cudaStreamWaitEvent(st, rest_ready, 0));
+        rest_ready = nullptr;
+      }
       const int r = launch_chunk(ctx, g, st, x, S, W, w0, std::min(wc, W - w0), cells, out, capacity, d_count,
                                  profiling, sel_pending);
       if (r != ATLAS_OK) return r;
     }
   }
+  if (rest_ready) CK(cudaStreamWaitEvent(st, rest_ready, 0));  // the refinement reads the whole stream
   if (sel_pending) CK(cudaStreamWaitEvent(st, ctx->ev_sel, 0));  // every selection joins the caller's stream
   const int r = launch_refine_all(ctx, st, x, S, out, capacity, d_count);
   if (r == ATLAS_OK && profiling && capacity > 0) ctx->prof_launches += 1;
@@ -594,8 +606,34 @@ int atlas_acq_run_host(atlas_acq_t ctx, void* stream, const float* h_iq, int64_t
   if (!ctx->d_stage_count) {
     if (cudaMalloc((void**)&ctx->d_stage_count, sizeof(int)) != cudaSuccess) return ATLAS_ERR_NO_MEMORY;
   }
-  CK(cudaMemcpyAsync(ctx->d_stage, h_iq, sizeof(float2) * (size_t)n_samples, cudaMemcpyHostToDevice, st));
-  const int r = run_impl(ctx, st, ctx->d_stage, n_samples, nullptr, ctx->d_stage_out, capacity, ctx->d_stage_count);
+  // The first launch group's samples go on the caller's stream; the rest on a
+  // copy stream, overlapping that group's transforms (its later groups and the
+  // refinement wait for the copy).  The copy stream first waits for the
+  // caller's earlier work, which may still read the staging buffer.
+  const Group& g0 = ctx->groups[0];
+  int wc0 = std::max(1, std::min<int>(ctx->wc_max, (int)(ctx->G_elems / ((size_t)ctx->K * g0.N))));
+  if (g0.wc > 0) wc0 = std::min(wc0, g0.wc);
+  const int64_t head = std::min<int64_t>(n_samples, (int64_t)(std::min(wc0, g0.windows(n_samples)) - 1) * g0.hop + g0.N);
+  const float2* h2 = reinterpret_cast<const float2*>(h_iq);
+  cudaEvent_t rest = nullptr;
+  if (head < n_samples) {
+    if (!ctx->copy_st) {
+      CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ctx->ev_copy_in, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_copy_done, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(ctx->ev_copy_in, st));
+    CK(cudaStreamWaitEvent(ctx->copy_st, ctx->ev_copy_in, 0));
+    CK(cudaMemcpyAsync(ctx->d_stage, h2, sizeof(float2) * (size_t)head, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_stage + head, h2 + head, sizeof(float2) * (size_t)(n_samples - head),
+                       cudaMemcpyHostToDevice, ctx->copy_st));
+    CK(cudaEventRecord(ctx->ev_copy_done, ctx->copy_st));
+    rest = ctx->ev_copy_done;
+  } else {
+    CK(cudaMemcpyAsync(ctx->d_stage, h_iq, sizeof(float2) * (size_t)n_samples, cudaMemcpyHostToDevice, st));
+  }
+  const int r = run_impl(ctx, st, ctx->d_stage, n_samples, nullptr, ctx->d_stage_out, capacity, ctx->d_stage_count,
+                         -1, rest);
   if (r != ATLAS_OK) return r;
   CK(cudaMemcpyAsync(h_count, ctx->d_stage_count, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
