@@ -54,6 +54,63 @@ __device__ __forceinline__ int valid_lags(const CorrParams& p, int w) {
   return nvalid;
 }
 
+// The index of a correlation item in the mixed radix (h: 2 for split rows,
+// else 1; rho: sps; bin: K; code: Cg; then the window of the launch group,
+// or the listed pair), kept as digits.  Advancing by the grid stride adds
+// digit by digit with one carry each: the item loop needs no integer
+// division (sps is a power of two).
+struct ItemCursor {
+  int h, rho, k, c;
+  int64_t w;
+  __device__ __forceinline__ void set(const CorrParams& p, bool split, int lsps, int64_t v) {
+    h = split ? (int)(v & 1) : 0;
+    if (split) v >>= 1;
+    rho = (int)(v & ((1 << lsps) - 1));
+    v >>= lsps;
+    k = p.pairs ? 0 : (int)(v % p.K);
+    if (!p.pairs) v /= p.K;
+    c = p.pairs ? 0 : (int)(v % p.Cg);
+    w = p.pairs ? v : v / p.Cg;
+  }
+  __device__ __forceinline__ void advance(const CorrParams& p, bool split, const ItemCursor& s) {
+    int cy = 0;
+    if (split) {
+      h += s.h;
+      cy = h >= 2;
+      h -= 2 * cy;
+    }
+    rho += s.rho + cy;
+    cy = rho >= p.sps;
+    rho -= cy * p.sps;
+    if (p.pairs) {
+      w += s.w + cy;
+      return;
+    }
+    k += s.k + cy;
+    cy = k >= p.K;
+    k -= cy * p.K;
+    c += s.c + cy;
+    cy = c >= p.Cg;
+    c -= cy * p.Cg;
+    w += s.w + cy;
+  }
+  // the item's window-spectrum row, window, code and partial-result index
+  __device__ __forceinline__ void locate(const CorrParams& p, int64_t& row, int& win, int& code, int64_t& out) const {
+    if (p.pairs) {
+      const int4 pr = p.pairs[w];
+      row = (int64_t)pr.x * p.sps + rho;
+      code = pr.y;
+      win = pr.z;
+      out = w * p.sps + rho;
+    } else {
+      row = (w * p.K + k) * p.sps + rho;
+      code = c;
+      win = p.w0 + (int)w;
+      out = ((w * p.Cg + c) * p.K + k) * p.sps + rho;
+    }
+  }
+};
+
 // Persistent over its rows (block b takes rows b, b + gridDim.x, ...).
 template <int LOGM, int LOGE>
 __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_window_fft(WindowFftParams p) {
@@ -101,34 +158,23 @@ __global__ void __launch_bounds__(fft_threads<LOGM, LOGE>()) k_corr(CorrParams p
   __syncthreads();
   build_tw32<LOGM>(sm_tw);
   const int64_t n_items = p.pairs ? (int64_t)p.n_pairs * sps : (int64_t)sps * p.K * p.nw * p.Cg;
-  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+  const int lsps = __ffs(sps) - 1;  // sps is a power of two
+  ItemCursor cur, stride;
+  cur.set(p, false, lsps, blockIdx.x);
+  stride.set(p, false, lsps, gridDim.x);
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x, cur.advance(p, false, stride)) {
     __syncthreads();  // tables ready; the previous cell's shared-memory reads are done
-    const int rho = (int)(item % sps);
-    const int64_t rest = item / sps;
+    const int rho = cur.rho;
     int64_t row, out;  // G row and partial-result index of this cell
     int c, w;
-    if (p.pairs) {     // listed (G row, code, window) cells
-      const int4 pr = p.pairs[rest];
-      row = (int64_t)pr.x * sps + rho;
-      c = pr.y;
-      w = pr.z;
-      out = rest * sps + rho;
-    } else {
-      const int k = (int)(rest % p.K);
-      const int z = (int)(rest / p.K);
-      const int wl = z / p.Cg;
-      c = z % p.Cg;
-      w = p.w0 + wl;
-      row = ((int64_t)wl * p.K + k) * sps + rho;
-      out = (((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho;
-    }
+    cur.locate(p, row, w, c, out);
     const int nvalid = valid_lags(p, w);
     const float2* G = p.G + row * FFT::M;
     const float2* D = p.D + (int64_t)c * FFT::M;
     auto load = [&](int i) { return cmul(G[i], D[i]); };
     // lag tau = sps*q + rho is valid iff q < qlim; a thread's outputs arrive in
     // increasing q, so the first maximum is the smallest lag
-    const int qlim = (nvalid - rho + sps - 1) / sps;
+    const int qlim = (nvalid - rho + sps - 1) >> lsps;
     float sum = 0.f, best = -1.f;
     int bq = 0x7fffffff;
     auto emit = [&](int q, float2 v) {
@@ -278,6 +324,10 @@ __global__ void __launch_bounds__(dif_threads<LOGM>(), 16 / dif_chunks<LOGM>()) 
   build_dif_tw<LOGM>(sm_tw);
 
   const int64_t n_items = (SPLIT ? 2 : 1) * (p.pairs ? (int64_t)p.n_pairs * sps : (int64_t)sps * p.K * p.nw * p.Cg);
+  const int lsps = __ffs(sps) - 1;  // sps is a power of two
+  ItemCursor cur, stride;
+  cur.set(p, SPLIT, lsps, blockIdx.x);
+  stride.set(p, SPLIT, lsps, gridDim.x);
   int64_t prev_out = -1;
   int par = 0;
   for (int64_t item = blockIdx.x;; item += gridDim.x) {
@@ -286,29 +336,13 @@ __global__ void __launch_bounds__(dif_threads<LOGM>(), 16 / dif_chunks<LOGM>()) 
     int rho = 0, qlim = 0, h = 0;
     float2 a[NP][NCH], b[NP][NCH];
     if (have) {
-      const int64_t it = SPLIT ? item >> 1 : item;
-      if (SPLIT) h = (int)(item & 1);
-      rho = (int)(it % sps);
-      const int64_t rest = it / sps;
+      h = cur.h;
+      rho = cur.rho;
       int64_t row;
       int c, w;
-      if (p.pairs) {
-        const int4 pr = p.pairs[rest];
-        row = (int64_t)pr.x * sps + rho;
-        c = pr.y;
-        w = pr.z;
-        out = rest * sps + rho;
-      } else {
-        const int k = (int)(rest % p.K);
-        const int z = (int)(rest / p.K);
-        const int wl = z / p.Cg;
-        c = z % p.Cg;
-        w = p.w0 + wl;
-        row = ((int64_t)wl * p.K + k) * sps + rho;
-        out = (((int64_t)wl * p.Cg + c) * p.K + k) * sps + rho;
-      }
+      cur.locate(p, row, w, c, out);
       const int nvalid = valid_lags(p, w);
-      qlim = (nvalid - rho + sps - 1) / sps;
+      qlim = (nvalid - rho + sps - 1) >> lsps;
       if (SPLIT) {  // lags q = 2 q' + h: count the q' with 2 q' + h < qlim
         qlim = qlim > h ? (qlim - h + 1) >> 1 : 0;
         out = 2 * out + h;
@@ -446,6 +480,7 @@ __global__ void __launch_bounds__(dif_threads<LOGM>(), 16 / dif_chunks<LOGM>()) 
     if (lane == 0) red[par * NCH + warp] = make_float4(sum, best, __int_as_float(bt), 0.f);
     prev_out = out;
     par ^= 1;
+    cur.advance(p, SPLIT, stride);
   }
 }
 
