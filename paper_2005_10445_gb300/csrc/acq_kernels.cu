@@ -17,14 +17,17 @@
 // memory for M <= 2^14.
 //
 // Kernels, in launch order per group of windows:
-//   k_code_bank   (create time) D_c = conj(FFT_M(chip_c)) / M
+//   k_code_bank   (create time) D_c = conj(FFT_M(chip_c)) / M; for M = 2^15 also
+//                 k_code_split_tables, the three half-length tables of the split form
 //   k_mix         per (tile, bins, w): read the window once, mix it for each bin
 //                 (one LO mix per bin, Section 3 step 2), box sum and decimate
 //                 by sps -> B[w][k][rho]
 //   k_window_fft  per (rho, k, w): G = FFT_M(B), in place
-//   k_corr        per (rho, k, w, c): G * D_c -> IFFT_M -> |.|^2 -> sum and
+//   k_corr_dif    per (rho, k, w, c): G * D_c -> IFFT_M -> |.|^2 -> sum and
 //                 argmax over the window's valid lags (Section 3 steps 7-8);
-//                 the correlation never leaves the chip
+//                 the correlation never leaves the chip (k_corr / k_corr_split:
+//                 the block-FFT forms for other sizes and tile shapes;
+//                 acq_fft_kernels.cuh)
 //   k_select      per (w, c): combine the sps partial results of each bin,
 //                 score = P_max / floor, best bin, threshold, ordered compaction
 //                 (one block; or k_select_pairs over many blocks into a
