@@ -82,8 +82,9 @@ typedef struct {
   int32_t split;           /* 1: run transforms of N/sps = 2^14 as two blocks of 2^13 (always done
                               for 2^15); 0 = default */
   int32_t precision;       /* 0: FP32 (default); 1 / 2: the per-code inverse transforms of codes with
-                              N/sps = 2^14 as radix-16 tensor-core contractions with FP16 / BF16
-                              operands, FP32 accumulation and per-stage power-of-two scaling
+                              N/sps = 2^14 as tensor-core (tcgen05) contractions, DFT stages of
+                              16, 32 and 32 points, with FP16 / BF16 operands, FP32 accumulation
+                              and per-stage power-of-two scaling
                               (other sizes stay FP32); window transforms and the refinement are
                               unchanged */
   int32_t reserved[2];
@@ -149,7 +150,9 @@ int atlas_acq_run_cells(atlas_acq_t ctx, void* stream, const float* d_iq, int64_
 /*
  * End-to-end form on HOST buffers: copies h_iq to the device, runs the search
  * and copies the count and the first min(count, capacity) detections back,
- * then synchronises `stream`.  h_iq, h_out and h_count are host memory (pinned
+ * then synchronises `stream`.  The samples past the first launch group are
+ * copied on a stream of the context's own, overlapping that group's work
+ * (ordered after the caller's earlier work on `stream`).  h_iq, h_out and h_count are host memory (pinned
  * memory makes the copies asynchronous DMA).  The device staging buffer for
  * the samples is allocated on first use for a given size and kept by the
  * context (Section 4.2 memoization); *h_count receives the full count.
