@@ -440,18 +440,18 @@ def run_learned(args, rank: int, world: int, dev, torch, dist) -> None:
         print(json.dumps(line), flush=True)
 
 
-def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
+def measure_precision(dev, torch, steps: int, warmup: int, cap: int, rank: int = 0):
     """Reduced-precision row: the realistic workload with the per-code inverse
     transforms in FP32 (CUDA cores) and as FP16 / BF16 tensor-core contractions;
     throughput, speedup over FP32, agreement of the detections and scores with
     the FP32 path, and the injected tags' cells found.  The errors against the
-    FP64 oracle are asserted by tests/test_gpu_precision.py."""
+    FP64 oracle are asserted by tests/test_gpu_precision.py.  Returns
+    ({precision: figures}, number of tag cells)."""
     import math
     from paper_2005_10445_gb300 import binding
     wl = make_workload(2 + rank)
     S = wl.n_samples
     x = torch.from_numpy(wl.iq().copy()).to(dev)
-    cap = args.capacity
     out = torch.empty(cap * 32, dtype=torch.uint8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -459,19 +459,19 @@ def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
     res, dets = {}, {}
     for prec in (0, 1, 2):
         srch = binding.Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len, precision=prec)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             srch.run_ptr(st.cuda_stream, x.data_ptr(), S, out.data_ptr(), cap, cnt.data_ptr())
         srch.profile_begin(65536)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize(dev)
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()
             evs[i][0].record(st)
             srch.run_ptr(st.cuda_stream, x.data_ptr(), S, out.data_ptr(), cap, cnt.data_ptr())
             evs[i][1].record(st)
         torch.cuda.synchronize(dev)
         pr = srch.profile_end()
-        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
         n = int(cnt.item())
         d = out.cpu().numpy().view(binding.DETECTION_DTYPE)[: min(n, cap)].copy()
         dets[prec] = d
@@ -500,15 +500,23 @@ def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
             "tag_cells_found": len(tag_cells & set(got)) / max(len(tag_cells), 1),
             "max_score_rel_diff_vs_fp32": max(score_diff or [0.0]),
             "max_toa_diff_vs_fp32": max(toa_diff or [0.0])})
+    return res, len(tag_cells)
+
+
+PRECISION_NAMES = {0: "fp32", 1: "fp16-tc", 2: "bf16-tc"}
+
+
+def run_precision(args, rank: int, world: int, dev, torch, dist) -> None:
+    res, n_tags = measure_precision(dev, torch, args.steps, args.warmup, args.capacity, rank)
     if rank == 0:
-        names = {0: "fp32", 1: "fp16-tc", 2: "bf16-tc"}
+        names = PRECISION_NAMES
         line = {"metric": METRIC, "value": res[1]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": res[1]["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f16 tensor-core contractions, f32 accumulate",
                 "data": "synthetic",
                 "config": {"workload": "precision: " + workload_name(),
                            "l2": "flushed before each step (256 MiB write), outside the timed events",
-                           "tag_cells": f"{len(tag_cells)} (code, window, lag, bin) cells of the injected tags"},
+                           "tag_cells": f"{n_tags} (code, window, lag, bin) cells of the injected tags"},
                 "per_precision": {names[p]: r for p, r in res.items()}}
         print(json.dumps(line), flush=True)
 
@@ -805,6 +813,7 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-unfused", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--no-batching", action="store_true", help="skip the batching figure of the default line")
+    ap.add_argument("--no-precision", action="store_true", help="skip the reduced-precision figure of the default line")
     ap.add_argument("--capacity", type=int, default=4096)
     ap.add_argument("--fsk-fft-len", type=int, default=1 << 18,
                     help="FSK workload: N (0 = the library default, 2 nextpow2(L) = 2^17 here)")
@@ -959,6 +968,16 @@ def main() -> None:
                             "kernels_per_graph_launch": r["kernels_per_launch"],
                             "executed_tflops": r["tflops"], "frac_of_fp32_peak": r["tflops"] / FP32_PEAK_TFLOPS,
                             "detections_per_stream": r["counts"], "clocks": r["clocks"]}
+    if world == 1 and not args.no_precision:
+        # the reduced-precision row on the same workload shape: FP32 against the
+        # FP16 / BF16 tensor-core correlation (3 timed runs each)
+        res, n_tags = measure_precision(dev, torch, 3, 2, args.capacity)
+        line["precision"] = {
+            "workload": "precision: " + workload_name(), "unit": UNIT,
+            "tag_cells": n_tags,
+            "per_precision": {PRECISION_NAMES[p]: {k: r[k] for k in (
+                "value", "k_corr_ms_per_launch", "speedup_vs_fp32", "detections", "fp32_detections_reproduced",
+                "tag_cells_found", "max_score_rel_diff_vs_fp32", "max_toa_diff_vs_fp32")} for p, r in res.items()}}
     if world == 1 and not args.no_cpu_baseline:
         # about 15 s on every host core of the GPU machine (16 Arm cores): 48 windows x every code and bin
         windows = tuple(range(1, 49))
