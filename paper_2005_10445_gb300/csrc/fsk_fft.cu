@@ -33,6 +33,7 @@
 #include <limits.h>
 
 #include "acq_common.cuh"
+#include "acq_fft_kernels.cuh"
 #include "fsk_internal.h"
 
 namespace atlas {
@@ -303,10 +304,100 @@ __global__ void __launch_bounds__(fsk_fft_threads<LOGM>(), fsk_min_blocks<LOGM, 
   FFT::run(sm, sm_tw, load, emit);
 }
 
-template <int LOGM, int R>
+// Pass A for M = 2^14, R = 16 with the warp-private inverse transform of
+// k_corr_dif (decimation in frequency, 16 chunks of 1024 points; see
+// acq_fft_kernels.cuh): persistent over the units (local item, rank).  Step A
+// (whole block) takes the 16-point DFTs of the columns j = t and t + 512 and
+// the twiddles W_M^{j m'}; step B (warp m' alone) transforms chunk m' with two
+// radix-32 passes.  Output m = m' + 16 k gets W_N^{m r} = W_N^{(m' + 16 lane) r}
+// W_512^{(r' r) mod 512} (k = lane + 32 r') and goes to scratch position
+// m' 1024 + k, one contiguous run per warp: the chunk order that
+// k_fsk_corr_b<14, 16, true> reads.
+constexpr size_t fsk_dif_smem() {
+  return sizeof(float2) * ((size_t)16 * kDifChunkPad + TwTables<14>::N + 32 * kDifTwPitch + 512);
+}
+
+__global__ void __launch_bounds__(512, 1) k_fsk_corr_a_dif(FskCorrParams p, int item0, int n_units) {
+  constexpr int LOGM = 14, M = 1 << LOGM, R = 16, N = M * R, LOGN = 18;
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float2* sm_tw = sm + 16 * kDifChunkPad;
+  const float2* trow = sm_tw + TwTables<LOGM>::N + kDifTwPitch * (threadIdx.x & 31);  // W_1024^{lane r}
+  float2* t512 = sm_tw + TwTables<LOGM>::N + 32 * kDifTwPitch;  // W_N^{512 i} = W_512^i
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  load_tables<LOGM>(sm_tw, p.tw);
+  __syncthreads();
+  build_dif_tw<LOGM>(sm_tw);
+  for (int i = t; i < 512; i += blockDim.x) t512[i] = twiddle<LOGN, +1>(p.twN, i << 9);
+  for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int local = u >> 4, rank = u & 15;
+    const int item = item0 + local;
+    const int pr = item / p.Cg, c = item % p.Cg;
+    const float2* X = p.X + (int64_t)pr * N + (int64_t)rank * M;
+    const float2* C = p.C + (int64_t)(p.sel ? p.sel[c] : c) * N + (int64_t)rank * M;
+    float2 a[16], b[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      a[m] = cmul(X[t + 1024 * m], C[t + 1024 * m]);
+      b[m] = cmul(X[t + 512 + 1024 * m], C[t + 512 + 1024 * m]);
+    }
+    dft_reg<16, +1>(a);
+    dft_reg<16, +1>(b);
+    {  // W_M^{t m'} and W_M^{(t + 512) m'} = W_M^{t m'} W_32^{m'}
+      const float2 wt1 = twiddle<LOGM, +1>(sm_tw, t), wt8 = twiddle<LOGM, +1>(sm_tw, 8 * t);
+      float2 wt = wt1;
+#define ATLAS_FSK_TW(M_)                                                               \
+  if (M_ > 1) wt = (M_) == 8 ? wt8 : cmul(wt, wt1);                                   \
+  a[M_] = cmul(a[M_], wt);                                                             \
+  b[M_] = cmul(b[M_], cmul(wt, make_float2(Tw<M_, 32, +1>::re, Tw<M_, 32, +1>::im)));
+      ATLAS_FSK_TW(1) ATLAS_FSK_TW(2) ATLAS_FSK_TW(3) ATLAS_FSK_TW(4) ATLAS_FSK_TW(5) ATLAS_FSK_TW(6)
+      ATLAS_FSK_TW(7) ATLAS_FSK_TW(8) ATLAS_FSK_TW(9) ATLAS_FSK_TW(10) ATLAS_FSK_TW(11) ATLAS_FSK_TW(12)
+      ATLAS_FSK_TW(13) ATLAS_FSK_TW(14) ATLAS_FSK_TW(15)
+#undef ATLAS_FSK_TW
+    }
+    __syncthreads();  // (1) the previous unit's chunks are read (and the tables are ready)
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      sm[m * kDifChunkPad + dif_pos(t)] = a[m];
+      sm[m * kDifChunkPad + dif_pos(t + 512)] = b[m];
+    }
+    __syncthreads();  // (2) every chunk is complete
+    float2* ch = sm + warp * kDifChunkPad;
+    float2 x[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) x[r] = ch[dif_pos(lane + 32 * r)];
+    __syncwarp();
+    dft_reg<32, +1>(x);
+    float4* rowp = reinterpret_cast<float4*>(ch + dif_pos(32 * lane));
+#pragma unroll
+    for (int r = 0; r < 32; r += 2) rowp[r / 2] = make_float4(x[r].x, x[r].y, x[r + 1].x, x[r + 1].y);
+    __syncwarp();
+    const float4* tw2 = reinterpret_cast<const float4*>(trow);
+#pragma unroll
+    for (int r = 0; r < 32; r += 2) {
+      const float4 w = tw2[r / 2];  // W_1024^{lane r}, W_1024^{lane (r + 1)} (forward: conjugated here)
+      x[r] = ch[dif_pos(lane + 32 * r)];
+      x[r + 1] = ch[dif_pos(lane + 32 * (r + 1))];
+      if (r > 0) x[r] = cmul_conj(x[r], make_float2(w.x, w.y));
+      x[r + 1] = cmul_conj(x[r + 1], make_float2(w.z, w.w));
+    }
+    dft_reg<32, +1>(x);
+    // m = warp + 16 (lane + 32 r): twiddle W_N^{m rank}, chunk-ordered store
+    const float2 base = twiddle<LOGN, +1>(p.twN, (warp + 16 * lane) * rank);
+    float2* out = p.scratch + ((int64_t)local * R + rank) * M + warp * 1024 + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) __stcs(out + 32 * r, cmul(x[r], cmul(base, t512[(r * rank) & 511])));
+  }
+}
+
+// CHUNKED: pass A wrote the scratch in the chunk order of the warp-private
+// transform (M = 2^14, R = 16: position m' 1024 + k holds m = m' + 16 k), so
+// block rho's positions [rho 1024, rho 1024 + 1024) are the m = 16 j + rho.
+template <int LOGM, int R, bool CHUNKED = false>
 __global__ void __launch_bounds__(256) k_fsk_corr_b(FskCorrParams p, int item0) {
   constexpr int M = 1 << LOGM;
   constexpr int MR = M / R;
+  static_assert(!CHUNKED || (LOGM == 14 && R == 16), "chunk order of 16 x 1024 points");
   __shared__ float4 red[64];
   const int local = blockIdx.x / R;
   const int rank = blockIdx.x % R;
@@ -320,10 +411,11 @@ __global__ void __launch_bounds__(256) k_fsk_corr_b(FskCorrParams p, int item0) 
   float s0 = 0.f, b0 = -1.f, s1 = 0.f, b1 = -1.f;
   int t0 = INT_MAX, t1 = INT_MAX;
   for (int j = threadIdx.x; j < MR; j += blockDim.x) {
-    const int m = rank * MR + j;
+    const int pos = rank * MR + j;
+    const int m = CHUNKED ? 16 * j + rank : pos;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = __ldcs(src + (int64_t)r * M + m);
+    for (int r = 0; r < R; ++r) v[r] = __ldcs(src + (int64_t)r * M + pos);
     dft_reg<R, +1>(v);
 #pragma unroll
     for (int n2 = 0; n2 < R; ++n2) {
@@ -377,6 +469,11 @@ cudaError_t prepare_one() {
     if ((e = cudaFuncSetAttribute(k_fsk_corr_a<LOGM, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
         cudaSuccess)
       return e;
+    if constexpr (LOGM == 14 && R == 16) {
+      if ((e = cudaFuncSetAttribute(k_fsk_corr_a_dif, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)fsk_dif_smem())) != cudaSuccess)
+        return e;
+    }
   }
   return cudaSuccess;
 }
@@ -433,10 +530,26 @@ cudaError_t corr_one(const FskCorrParams& p, cudaStream_t s) {
       if (p.chunk_items < 1) return cudaErrorInvalidValue;
       for (int i0 = 0; i0 < items; i0 += p.chunk_items) {
         const int n = std::min(p.chunk_items, items - i0);
-        k_fsk_corr_a<LOGM, R><<<n * R, fsk_fft_threads<LOGM>(), fsk_fft_smem<LOGM, LOGN>(), s>>>(p, i0);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        k_fsk_corr_b<LOGM, R><<<n * R, 256, 0, s>>>(p, i0);
+        cudaError_t e;
+        if constexpr (LOGM == 14 && R == 16) {
+          static int resident = 0;  // blocks of k_fsk_corr_a_dif resident on the device
+          if (resident == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+                (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+                (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsk_corr_a_dif, 512, fsk_dif_smem())) !=
+                    cudaSuccess)
+              return e;
+            resident = std::max(1, per_sm) * sms;
+          }
+          k_fsk_corr_a_dif<<<std::min(n * R, resident), 512, fsk_dif_smem(), s>>>(p, i0, n * R);
+          if ((e = cudaGetLastError()) != cudaSuccess) return e;
+          k_fsk_corr_b<LOGM, R, true><<<n * R, 256, 0, s>>>(p, i0);
+        } else {
+          k_fsk_corr_a<LOGM, R><<<n * R, fsk_fft_threads<LOGM>(), fsk_fft_smem<LOGM, LOGN>(), s>>>(p, i0);
+          if ((e = cudaGetLastError()) != cudaSuccess) return e;
+          k_fsk_corr_b<LOGM, R><<<n * R, 256, 0, s>>>(p, i0);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
       }
       return cudaSuccess;
