@@ -195,6 +195,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc5(CorrParams p, int* sta
   fence_after();
   const uint32_t tmem = *tmem_slot;
   constexpr uint32_t id_a = idesc<PREC>(128, 32), id_b = idesc<PREC>(128, 64);
+  // hop <= N/2: no valid lag has output r >= 16 of stage B2, which then forms
+  // only outputs 0..15 (N = 32: the first 32 rows of the DFT matrix); the
+  // floor's sum comes from B2's FP32 inputs by Parseval (sum |X|^2 = 32 sum |x|^2)
+  const bool half = 2 * p.hop <= p.N;
 
   const int sps = p.sps;
   const int64_t n_items = p.pairs ? (int64_t)p.n_pairs * sps : (int64_t)sps * p.K * p.nw * p.Cg;
@@ -355,7 +359,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc5(CorrParams p, int* sta
     }
 
     // ---- stage B2: the warp's 32 x 32 block transposed (row r', column l), one scale per warp
+    float energy = 0.f;  // sum of |x|^2 over this thread's B2 inputs (half)
     {
+      if (half) {
+        float e0 = 0.f, e1 = 0.f;
+#pragma unroll
+        for (int r = 0; r < 32; r += 2) {
+          e0 = fmaf(x[r].x, x[r].x, fmaf(x[r].y, x[r].y, e0));
+          e1 = fmaf(x[r + 1].x, x[r + 1].x, fmaf(x[r + 1].y, x[r + 1].y, e1));
+        }
+        energy = 32.f * (e0 + e1);
+      }
       float mx = 0.f;
 #pragma unroll
       for (int r = 0; r < 32; ++r) mx = fmaxf(mx, fmaxf(fabsf(x[r].x), fabsf(x[r].y)));
@@ -375,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc5(CorrParams p, int* sta
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
           mma(tmem + 64 * g, desc(base + kOffOpnd + g * kB2Bytes + 288 * kk, 144, 1152),
-              desc(base + kOffFB + 256 * kk, 128, 1024), id_b, kk);
+              desc(base + kOffFB + 256 * kk, 128, 1024), half ? id_a : id_b, kk);
         commit(&bars[5 + g]);
       }
       if (!wait_bar(&bars[5 + g], ph)) *abort_flag = 1;
@@ -385,26 +399,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc5(CorrParams p, int* sta
       tmem_ld32(ta, v);
 #pragma unroll
       for (int r = 0; r < 16; ++r) x[r] = make_float2(v[2 * r] * u2, v[2 * r + 1] * u2);
-      tmem_ld32(ta + 32, v);
+      if (!half) {
+        tmem_ld32(ta + 32, v);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) x[16 + r] = make_float2(v[2 * r] * u2, v[2 * r + 1] * u2);
+        for (int r = 0; r < 16; ++r) x[16 + r] = make_float2(v[2 * r] * u2, v[2 * r + 1] * u2);
+      }
     }
 
     // ---- epilogue: lag tau = sps q + rho with q = warp + 16 (lane + 32 r), increasing in r
     float s0 = 0.f, s1 = 0.f, best = -1.f;
     int bq = 0x7fffffff;
     const int q0 = warp + 16 * lane;
+    float sum;
+    if (half) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const float P = fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
-      if (r & 1) s1 += P;
-      else s0 += P;
-      if (q0 + 512 * r < qlim && P > best) {
-        best = P;
-        bq = q0 + 512 * r;
+      for (int r = 0; r < 16; ++r) {
+        const float P = fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
+        if (q0 + 512 * r < qlim && P > best) {
+          best = P;
+          bq = q0 + 512 * r;
+        }
       }
+      sum = energy;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const float P = fmaf(x[r].x, x[r].x, x[r].y * x[r].y);
+        if (r & 1) s1 += P;
+        else s0 += P;
+        if (q0 + 512 * r < qlim && P > best) {
+          best = P;
+          bq = q0 + 512 * r;
+        }
+      }
+      sum = s0 + s1;
     }
-    float sum = s0 + s1;
     int bt = bq == 0x7fffffff ? bq : bq * sps + rho;
     warp_reduce_stats(sum, best, bt);
     if (lane == 0) red[warp] = make_float4(sum, best, __int_as_float(bt), 0.f);
