@@ -199,14 +199,29 @@ def test_repeat_runs_bit_identical(torch_cuda):
     assert a[0].tobytes() == b[0].tobytes() and a[2].tobytes() == b[2].tobytes()
 
 
-def test_host_buffer_entry_matches_device(torch_cuda):
-    wl = synth.small(seed=11)
+@pytest.mark.parametrize("case", ["one group", "groups of one window", "mixed code lengths"])
+def test_host_buffer_entry_matches_device(torch_cuda, case):
+    """The host-buffer entry copies the first launch group's samples on the
+    caller's stream and the rest on a copy stream that the later groups (and
+    other code-length groups) wait for: its records equal the device entry's,
+    also when the stream spans several launch groups and several code
+    lengths, and when it runs twice in a row on the same staging buffer."""
     from paper_2005_10445_gb300.binding import Search
-    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len)
+    kw = {}
+    if case == "mixed code lengths":
+        wl = synth.batch(seed=3)[6]
+        wl = synth.Workload(wl.name, wl.x[: 600_000], wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, wl.fft_len,
+                            [t for t in wl.tags if t.delay + len(wl.chips[t.code]) * wl.sps <= 600_000], wl.sigma)
+    else:
+        wl = synth.small(seed=11)
+        if case == "groups of one window":
+            kw["windows_per_launch"] = 1
+    s = Search(wl.chips, wl.sps, wl.fs_hz, wl.freqs_hz, fft_len=wl.fft_len, **kw)
     x = torch_cuda.from_numpy(wl.iq().copy()).cuda()
     d_dev, n_dev, _ = s.run(x)
-    d_host, n_host = s.run_host(wl.iq())
-    assert n_dev == n_host and d_dev.tobytes() == d_host.tobytes()
+    for _ in range(2):
+        d_host, n_host = s.run_host(wl.iq())
+        assert n_dev == n_host and d_dev.tobytes() == d_host.tobytes()
 
 
 def test_windows_per_launch_does_not_change_results(torch_cuda):
