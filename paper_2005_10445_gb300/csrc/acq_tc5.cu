@@ -227,25 +227,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc5(CorrParams p, int* sta
     const float2* G = p.G + row * (1 << kLogM);
     const float2* D = p.D + (int64_t)c * (1 << kLogM);
 
-    // ---- stage A operand: rows j = 2t and 2t + 1 (16-byte loads of two adjacent
-    // columns), each scaled by a power of two
+    // ---- stage A operand: rows j = t and jb = 1024 - t (thread 0: 0 and 512),
+    // each scaled by a power of two.  The code spectrum of +/-1 chips is
+    // Hermitian and M - (j + 1024 m) = jb + 1024 (15 - m): row jb takes row j's
+    // code spectrum reversed and conjugated, so a thread loads one column of
+    // it (a quarter fewer bytes from L2 than two columns)
     {
-      const float4* G4 = reinterpret_cast<const float4*>(G);
-      const float4* D4 = reinterpret_cast<const float4*>(D);
+      const int jb = t ? 1024 - t : 512, jd = t ? t : 512;
       float2 z0[16], z1[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) z0[m] = D[jd + 1024 * m];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) z1[m] = cmul_conj(G[jb + 1024 * m], z0[15 - m]);
+      if (t == 0) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) z0[m] = D[1024 * m];
+      }
       float mx0 = 0.f, mx1 = 0.f;
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const float4 gv = G4[t + 512 * m], dv = D4[t + 512 * m];
-        z0[m] = cmul(make_float2(gv.x, gv.y), make_float2(dv.x, dv.y));
-        z1[m] = cmul(make_float2(gv.z, gv.w), make_float2(dv.z, dv.w));
+        z0[m] = cmul(G[t + 1024 * m], z0[m]);
         mx0 = fmaxf(mx0, fmaxf(fabsf(z0[m].x), fabsf(z0[m].y)));
         mx1 = fmaxf(mx1, fmaxf(fabsf(z1[m].x), fabsf(z1[m].y)));
       }
       float s0, u0, s1, u1;
       pow2_scale(mx0, s0, u0);
       pow2_scale(mx1, s1, u1);
-      *reinterpret_cast<float2*>(undo_a + 2 * t) = make_float2(u0, u1);
+      undo_a[t] = u0;
+      undo_a[jb] = u1;
 #pragma unroll
       for (int kg = 0; kg < 4; ++kg) {
         uint4 v;
@@ -253,12 +262,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc5(CorrParams p, int* sta
         v.y = pack2<PREC>(z0[4 * kg + 1].x * s0, z0[4 * kg + 1].y * s0);
         v.z = pack2<PREC>(z0[4 * kg + 2].x * s0, z0[4 * kg + 2].y * s0);
         v.w = pack2<PREC>(z0[4 * kg + 3].x * s0, z0[4 * kg + 3].y * s0);
-        *reinterpret_cast<uint4*>(opnd + off_a(2 * t, kg)) = v;
+        *reinterpret_cast<uint4*>(opnd + off_a(t, kg)) = v;
         v.x = pack2<PREC>(z1[4 * kg].x * s1, z1[4 * kg].y * s1);
         v.y = pack2<PREC>(z1[4 * kg + 1].x * s1, z1[4 * kg + 1].y * s1);
         v.z = pack2<PREC>(z1[4 * kg + 2].x * s1, z1[4 * kg + 2].y * s1);
         v.w = pack2<PREC>(z1[4 * kg + 3].x * s1, z1[4 * kg + 3].y * s1);
-        *reinterpret_cast<uint4*>(opnd + off_a(2 * t + 1, kg)) = v;
+        *reinterpret_cast<uint4*>(opnd + off_a(jb, kg)) = v;
       }
     }
     fence_async();
