@@ -293,20 +293,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc5(CorrParams p, int* sta
       const int j = 128 * i + 32 * q + lane;
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32 * i, v);
-      // the row's scale is undone inside the twiddle: wt = u W_M^{j m}
+      // the row's scale is undone inside the twiddle: wt = u W_M^{j m}, by
+      // repeated multiplication (15 steps: a few FP32 ulps, far below the
+      // operands' FP16 / BF16 rounding)
       const float u = undo_a[j];
       const float2 w1 = twiddle<kLogM, +1>(sm_tw, j);
       float2 wt = make_float2(u, 0.f);
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        if (m > 0) {
-          if ((m & 7) == 0) {
-            const float2 wm = twiddle<kLogM, +1>(sm_tw, j * m);
-            wt = make_float2(wm.x * u, wm.y * u);
-          } else {
-            wt = cmul(wt, w1);
-          }
-        }
+        if (m > 0) wt = cmul(wt, w1);
         chunks[m * 1024 + j] = cmul(make_float2(v[2 * m], v[2 * m + 1]), wt);
       }
     }
