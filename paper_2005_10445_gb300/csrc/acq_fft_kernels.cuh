@@ -270,12 +270,13 @@ __device__ __forceinline__ void warp_reduce_stats(float& sum, float& best, int& 
 
 // Step A's twiddles for output m' = MP of the column pair (j, 1024 - j):
 // W_M^{j m'} for column j and its conjugate for the mirror column (after the
-// shift of its DFT inputs); W_M^{j m'} from the tables every eighth m' and by
-// repeated multiplication between.
+// shift of its DFT inputs); W_M^{j m'} by repeated multiplication with W_M^j
+// (at most 15 steps, a few FP32 ulps; a table read at m' = 8 would be an
+// 8-way bank conflict, the lanes' indices 8 j being 64 bytes apart).
 template <int LOGM, int MP>
 __device__ __forceinline__ void dif_twiddle_one(float2* a, float2* b, float2& wt, const float2& wt1,
                                                 const float2* tw, int j) {
-  if constexpr (MP > 1) wt = (MP & 7) == 0 ? twiddle<LOGM, +1>(tw, j * MP) : cmul(wt, wt1);
+  if constexpr (MP > 1) wt = cmul(wt, wt1);
   a[MP] = cmul(a[MP], wt);
   b[MP] = cmul_conj(b[MP], wt);
 }
