@@ -979,7 +979,7 @@ def main() -> None:
                 "value", "k_corr_ms_per_launch", "speedup_vs_fp32", "detections", "fp32_detections_reproduced",
                 "tag_cells_found", "max_score_rel_diff_vs_fp32", "max_toa_diff_vs_fp32")} for p, r in res.items()}}
     if world == 1 and not args.no_cpu_baseline:
-        # about 15 s on every host core of the GPU machine (16 Arm cores): 48 windows x every code and bin
+        # about 15 s on 16 Arm host cores: 48 windows x every code and bin
         windows = tuple(range(1, 49))
         with oracle_pool(wl) as pool:
             dt, samples = oracle_sample(pool, wl, windows=windows)

@@ -1,4 +1,4 @@
-"""Training and evaluation driver of the learned (code, bin) proposal.
+"""Training and evaluation loop of the learned (code, bin) proposal.
 
 Host-side orchestration only: every step (exhaustive labelling search,
 features, forward, backward, Adam, candidate selection, proposal search) runs

@@ -1,4 +1,4 @@
-"""The oracle's process-pool driver gives exactly the single-process search:
+"""The oracle's process-pool search gives exactly the single-process search:
 the same detections in the same order and the same cells (CPU only)."""
 from oracle import acq, parallel
 from paper_2005_10445_gb300 import synth
