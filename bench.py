@@ -84,7 +84,7 @@ def fsk_kernel_source_hash() -> str:
     """sha256 (first 16 hex digits) of the FSK correlation's kernel sources and
     of the host file that sizes its passes."""
     h = hashlib.sha256()
-    for f in ("fsk_fft.cu", "acq_common.cuh", "fft_block.cuh", "atlas_fsk_host.cu"):
+    for f in ("fsk_fft.cu", "acq_fft_kernels.cuh", "acq_common.cuh", "fft_block.cuh", "atlas_fsk_host.cu"):
         with open(os.path.join(ROOT, "paper_2005_10445_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

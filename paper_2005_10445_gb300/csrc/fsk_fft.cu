@@ -343,11 +343,13 @@ __global__ void __launch_bounds__(512, 1) k_fsk_corr_a_dif(FskCorrParams p, int 
     }
     dft_reg<16, +1>(a);
     dft_reg<16, +1>(b);
-    {  // W_M^{t m'} and W_M^{(t + 512) m'} = W_M^{t m'} W_32^{m'}
-      const float2 wt1 = twiddle<LOGM, +1>(sm_tw, t), wt8 = twiddle<LOGM, +1>(sm_tw, 8 * t);
+    {  // W_M^{t m'} and W_M^{(t + 512) m'} = W_M^{t m'} W_32^{m'}; W_M^{t m'} by
+       // repeated multiplication with W_M^t (a table read of W_M^{8 t} would be
+       // an 8-way bank conflict)
+      const float2 wt1 = twiddle<LOGM, +1>(sm_tw, t);
       float2 wt = wt1;
 #define ATLAS_FSK_TW(M_)                                                               \
-  if (M_ > 1) wt = (M_) == 8 ? wt8 : cmul(wt, wt1);                                   \
+  if (M_ > 1) wt = cmul(wt, wt1);                                                      \
   a[M_] = cmul(a[M_], wt);                                                             \
   b[M_] = cmul(b[M_], cmul(wt, make_float2(Tw<M_, 32, +1>::re, Tw<M_, 32, +1>::im)));
       ATLAS_FSK_TW(1) ATLAS_FSK_TW(2) ATLAS_FSK_TW(3) ATLAS_FSK_TW(4) ATLAS_FSK_TW(5) ATLAS_FSK_TW(6)
